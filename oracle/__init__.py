@@ -1,0 +1,269 @@
+"""Plain FP64 CPU oracle of ADOP's one-pixel point rasterizer (Sec. 3.1, 3.3).
+
+TEST INFRASTRUCTURE ONLY.  This package is the independent checker of the
+CUDA library: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference arm of ``bench.py`` may import it.  It shares no code with
+``paper_2110_06635_gb300`` and imports nothing from it; cameras and scenes are
+read by duck typing (attributes ``w, h, fx, fy, cx, cy, k1, k2, k3, p1, p2, R,
+t``), so the seeded generators in ``scenes`` can feed both sides.
+
+The arithmetic lives in ``adop_oracle.c`` (compiled with ``-ffp-contract=off``
+so that the FP32 projection contract is evaluated one IEEE operation at a
+time).  This module only marshals numpy arrays.  A pure-Python list-based
+brute-force renderer (``bruteforce``) restates Eq. blend and Eq. spatialderiv
+with explicit per-pixel point lists, for tiny scenes.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "adop_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into ``oracle/liboracle.so`` (gcc, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+             "-fno-math-errno", "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Intr(ct.Structure):
+    _fields_ = [("w", ct.c_int32), ("h", ct.c_int32)] + [
+        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")]
+
+
+class _Pose(ct.Structure):
+    _fields_ = [("R", ct.c_float * 9), ("t", ct.c_float * 3)]
+
+
+_P = ct.c_void_p
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ct.CDLL(build())
+        lib.orc_project_f32.argtypes = [_P, _P, _P, _P, _P, _P]
+        lib.orc_pixel.argtypes = [ct.c_float, ct.c_float, ct.c_int, ct.c_int32, ct.c_int32, _P, _P]
+        lib.orc_pixel.restype = ct.c_int
+        lib.orc_pyramid_pixels.argtypes = [ct.c_int32, ct.c_int32, ct.c_int]
+        lib.orc_pyramid_pixels.restype = ct.c_int64
+        lib.orc_forward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P, ct.c_int32, ct.c_float,
+                                    ct.c_float, _P, _P, _P, _P, _P, _P]
+        lib.orc_forward.restype = ct.c_int
+        lib.orc_project_jac_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        lib.orc_camera_f64.argtypes = [_P, _P, _P]
+        lib.orc_camera_f64_many.argtypes = [ct.c_int64, _P, _P, _P]
+        lib.orc_backward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, ct.c_int32, ct.c_float,
+                                     _P, ct.c_int32, _P, _P, _P, _P, _P, _P,
+                                     _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.orc_backward.restype = ct.c_int
+        lib.orc_epilogue.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_double, _P, _P, _P,
+                                     _P, ct.c_int32, _P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _intr(cam) -> _Intr:
+    return _Intr(int(cam.w), int(cam.h), *[float(getattr(cam, k)) for k in
+                                           ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
+
+
+def _pose(cam) -> _Pose:
+    R = np.ascontiguousarray(np.asarray(cam.R, dtype=np.float32).reshape(9))
+    t = np.ascontiguousarray(np.asarray(cam.t, dtype=np.float32).reshape(3))
+    return _Pose((ct.c_float * 9)(*R.tolist()), (ct.c_float * 3)(*t.tolist()))
+
+
+def layer_shapes(w: int, h: int, levels: int):
+    """(h_l, w_l) of each pyramid layer: w_l = w >> l, h_l = h >> l."""
+    return [(h >> l, w >> l) for l in range(levels)]
+
+
+def split_layers(flat: np.ndarray, w: int, h: int, levels: int, c: int | None = None):
+    """Split a concatenated per-layer array into a list (planar c x h_l x w_l if c)."""
+    out, off = [], 0
+    for hl, wl in layer_shapes(w, h, levels):
+        n = hl * wl * (c or 1)
+        blk = flat[off:off + n]
+        out.append(blk.reshape((c, hl, wl) if c else (hl, wl)))
+        off += n
+    return out
+
+
+def project_f32(cam, x):
+    """FP32 projection contract for one point -> (u0, v0, z) as numpy float32."""
+    lib = _load()
+    xv = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(3))
+    out = np.zeros(3, dtype=np.float32)
+    K, T = _intr(cam), _pose(cam)
+    lib.orc_project_f32(ct.byref(K), ct.byref(T), _ptr(xv), _ptr(out[0:]), _ptr(out[1:]), _ptr(out[2:]))
+    return out[0], out[1], out[2]
+
+
+def pixel(u0, v0, l, w, h):
+    """Eq. round + Eq. boundscheck at layer l -> (pu, pv) or None."""
+    lib = _load()
+    pu, pv = ct.c_int32(), ct.c_int32()
+    ok = lib.orc_pixel(ct.c_float(u0), ct.c_float(v0), int(l), int(w), int(h), ct.byref(pu), ct.byref(pv))
+    return (pu.value, pv.value) if ok else None
+
+
+def project_jac_f64(cam, x):
+    """FP64 (u0, v0), X, d(u0,v0)/dX (2x3) and d(u0,v0)/d(fx,fy,cx,cy,k1,k2) (2x6)."""
+    lib = _load()
+    xv = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(3))
+    uv, X = np.zeros(2), np.zeros(3)
+    JX, JK = np.zeros(6), np.zeros(12)
+    K, T = _intr(cam), _pose(cam)
+    lib.orc_project_jac_f64(ct.byref(K), ct.byref(T), _ptr(xv), _ptr(uv), _ptr(X), _ptr(JX), _ptr(JK))
+    return uv, X, JX.reshape(2, 3), JK.reshape(2, 6)
+
+
+def camera_f64(k9, X):
+    """The camera model in FP64: k9 = (fx, fy, cx, cy, k1, k2, k3, p1, p2),
+    X camera-space point -> (u0, v0)."""
+    lib = _load()
+    k = np.ascontiguousarray(k9, dtype=np.float64).reshape(9)
+    Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(3)
+    uv = np.zeros(2)
+    lib.orc_camera_f64(_ptr(k), _ptr(Xv), _ptr(uv))
+    return uv
+
+
+def camera_f64_many(k9, X):
+    """camera_f64 over an n x 3 array of camera-space points -> n x 2."""
+    lib = _load()
+    k = np.ascontiguousarray(k9, dtype=np.float64).reshape(9)
+    Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    uv = np.zeros((Xv.shape[0], 2))
+    lib.orc_camera_f64_many(Xv.shape[0], _ptr(k), _ptr(Xv), _ptr(uv))
+    return uv
+
+
+@dataclass
+class Forward:
+    keys: np.ndarray   # uint64, concatenated pyramid
+    cnt: np.ndarray    # uint32
+    img: np.ndarray    # float64, concatenated planar c x h_l x w_l
+    pix: np.ndarray    # int32 n x levels (-1 = discarded)
+    z: np.ndarray      # float32 n
+    w: int
+    h: int
+    levels: int
+    c: int
+
+    def layer_keys(self):
+        return split_layers(self.keys, self.w, self.h, self.levels)
+
+    def layer_cnt(self):
+        return split_layers(self.cnt, self.w, self.h, self.levels)
+
+    def layer_img(self):
+        return split_layers(self.img, self.w, self.h, self.levels, self.c)
+
+
+def feat_to_f64(feat) -> np.ndarray:
+    """Exact upcast of stored features to FP64.  BF16 arrives as uint16 bit
+    patterns (the upper half of an IEEE binary32), FP16 as numpy float16."""
+    f = np.asarray(feat)
+    if f.dtype == np.uint16:
+        return (f.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return f.astype(np.float64)
+
+
+def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None) -> Forward:
+    """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend)."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    f64 = np.ascontiguousarray(feat_to_f64(feat))
+    n, c = f64.shape
+    assert xyz.shape == (n, 3)
+    npx = int(lib.orc_pyramid_pixels(int(cam.w), int(cam.h), int(levels)))
+    keys = np.empty(npx, dtype=np.uint64)
+    cnt = np.empty(npx, dtype=np.uint32)
+    img = np.empty(npx * c, dtype=np.float64)
+    pix = np.empty((n, levels), dtype=np.int32)
+    z = np.empty(n, dtype=np.float32)
+    bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
+    nrm = None if normals is None else np.ascontiguousarray(normals, dtype=np.float32)
+    K, T = _intr(cam), _pose(cam)
+    rc = lib.orc_forward(n, _ptr(xyz), c, _ptr(f64), _ptr(nrm), ct.byref(K), ct.byref(T), int(levels),
+                         ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(keys), _ptr(cnt), _ptr(img),
+                         _ptr(pix), _ptr(z))
+    if rc != 0:
+        raise MemoryError("oracle forward: allocation failed")
+    return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)
+
+
+@dataclass
+class Backward:
+    dfeat: np.ndarray
+    dxyz: np.ndarray
+    dpose: np.ndarray
+    dintr: np.ndarray
+    dpose_abs: np.ndarray
+    dintr_abs: np.ndarray
+    gu: np.ndarray
+    gv: np.ndarray
+
+
+def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_projected=False) -> Backward:
+    """Sec. 3.1's backward pass for one camera; G is dL/dI over the
+    concatenated pyramid (same layout as ``fwd.img``)."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    f64 = np.ascontiguousarray(feat_to_f64(feat))
+    n, c = f64.shape
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    assert G.shape == fwd.img.shape
+    dfeat = np.empty((n, c))
+    dxyz = np.empty((n, 3))
+    dpose, dintr, dpa, dia = (np.empty(6) for _ in range(4))
+    gu = np.empty((n, fwd.levels))
+    gv = np.empty((n, fwd.levels))
+    bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
+    K, T = _intr(cam), _pose(cam)
+    rc = lib.orc_backward(n, _ptr(xyz), c, _ptr(f64), ct.byref(K), ct.byref(T), fwd.levels,
+                          ct.c_float(alpha), _ptr(bg), int(bool(all_projected)), _ptr(fwd.keys),
+                          _ptr(fwd.cnt), _ptr(fwd.img), _ptr(fwd.pix), _ptr(fwd.z), _ptr(G),
+                          _ptr(dfeat), _ptr(dxyz), _ptr(dpose), _ptr(dintr), _ptr(dpa), _ptr(dia),
+                          _ptr(gu), _ptr(gv))
+    if rc != 0:
+        raise MemoryError("oracle backward: allocation failed")
+    return Backward(dfeat, dxyz, dpose, dintr, dpa, dia, gu, gv)
+
+
+def epilogue(img0, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0, 0.0), crf=None,
+             want_grad=False):
+    """Sec. 3.3 photometric model on a layer-0 image (c x h x w, FP64).
+    Returns the new image (and d out / d in if want_grad)."""
+    lib = _load()
+    img = np.array(img0, dtype=np.float64, copy=True, order="C")
+    c, h, w = img.shape
+    grad = np.empty_like(img) if want_grad else None
+    lut = None if crf is None else np.ascontiguousarray(crf, dtype=np.float64)
+    crf_n = 0 if crf is None else lut.shape[-1]
+    lib.orc_epilogue(w, h, c, _ptr(img), ct.c_double(ev), _ptr(np.asarray(wb, np.float64)),
+                     _ptr(np.asarray(vig_c, np.float64)), _ptr(np.asarray(vig_a, np.float64)),
+                     _ptr(lut), crf_n, _ptr(grad))
+    return (img, grad) if want_grad else img
+
+
+from .bruteforce import bruteforce_render, bruteforce_spatial  # noqa: E402,F401

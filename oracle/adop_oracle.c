@@ -1,0 +1,535 @@
+/*
+ * Plain CPU oracle of ADOP's differentiable one-pixel point rasterizer
+ * (Rueckert, Franke, Stamminger: "ADOP: Approximate Differentiable One-Pixel
+ * Point Rendering", Sec. 3.1, Eqs. render, round, boundscheck, normalculling,
+ * depthtest, blend, induce, gradp, spatialderiv, tangent; Sec. 3.3 for the
+ * photometric epilogue).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU path must compute.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA library; the two meet only in
+ * the written FP32 projection contract below and in seeded inputs.
+ *
+ * Precision rules
+ *   - The projection that decides a pixel and a depth is an FP32 contract:
+ *     every step is one IEEE binary32 operation in the order written below,
+ *     no fused multiply-add (compile with -ffp-contract=off), rounding to
+ *     the nearest integer with ties to even (nearbyintf under the default
+ *     rounding mode).  The paper leaves the precision open; this reading is
+ *     what makes depth/index buffers comparable bit for bit.
+ *   - Everything after the pixel/depth decision (blend sums, means, the
+ *     induced changes of Eq. spatialderiv, Jacobians, the chain rule and all
+ *     reductions) is FP64.
+ *   - Decisions that compare depths (fuzzy test, the cases of Eq.
+ *     spatialderiv) are taken in FP32, the precision of the depth buffer.
+ *
+ * Layouts (all per camera)
+ *   xyz     n x 3 float, world space
+ *   feat    n x c double (features upcast exactly from their storage type)
+ *   layers  l = 0..levels-1, w_l = w >> l, h_l = h >> l, pixel id within a
+ *           layer = pv * w_l + pu; per-layer arrays are concatenated in
+ *           layer order (offset of layer l = sum_{k<l} w_k h_k pixels)
+ *   image   per layer c x h_l x w_l (planar), concatenated
+ *   keys    per pixel: (bits(z_min) << 32) | index of the nearest point,
+ *           UINT64_MAX for an empty pixel
+ *
+ * parity pins: projection (closed forms), blend + spatial gradient (hand
+ * example, brute force, shift-and-rerender), chain rule (finite differences
+ * with an independent SE(3) exponential) -- see tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Camera model C: pinhole with Brown-Conrady distortion (k1,k2,k3 radial,
+ * p1,p2 tangential).  The paper's scenes use "Pinhole + Dist." (Table
+ * scenes) without stating the distortion polynomial; this is the common
+ * five-coefficient model. */
+typedef struct {
+    int32_t w, h;
+    float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+} orc_intrinsics;
+
+/* World-to-camera rigid transform (R, t), R row-major (Eq. render). */
+typedef struct {
+    float R[9];
+    float t[3];
+} orc_pose;
+
+/* ------------------------------------------------------------------ */
+/* FP32 projection contract (Sec. 3.1, P_l(C,R,t,x) = 2^-l C(Rx + t))   */
+/* ------------------------------------------------------------------ */
+
+/* X = R x + t, each row summed left to right, then t added. */
+static void transform_f32(const orc_pose* T, const float* x, float* X) {
+    for (int r = 0; r < 3; ++r) {
+        float s = T->R[3 * r + 0] * x[0];
+        s = s + T->R[3 * r + 1] * x[1];
+        s = s + T->R[3 * r + 2] * x[2];
+        X[r] = s + T->t[r];
+    }
+}
+
+/* Camera model C applied to a camera-space point; returns layer-0 pixel
+ * coordinates (u0, v0).  z = X[2] is the depth of Eq. depthtest. */
+static void camera_f32(const orc_intrinsics* K, const float* X, float* u0, float* v0) {
+    float xn = X[0] / X[2];
+    float yn = X[1] / X[2];
+    float r2 = xn * xn + yn * yn;
+    float d = 1.0f + r2 * (K->k1 + r2 * (K->k2 + r2 * K->k3));
+    float a = xn * yn;
+    float tx = (2.0f * K->p1) * a + K->p2 * (r2 + 2.0f * (xn * xn));
+    float ty = K->p1 * (r2 + 2.0f * (yn * yn)) + (2.0f * K->p2) * a;
+    float xd = xn * d + tx;
+    float yd = yn * d + ty;
+    *u0 = K->fx * xd + K->cx;
+    *v0 = K->fy * yd + K->cy;
+}
+
+/* Exported: the FP32 contract for one point (used by the projection pins). */
+void orc_project_f32(const orc_intrinsics* K, const orc_pose* T, const float* x,
+                     float* u0, float* v0, float* z) {
+    float X[3];
+    transform_f32(T, x, X);
+    camera_f32(K, X, u0, v0);
+    *z = X[2];
+}
+
+/* Eq. round + Eq. boundscheck for layer l.  The layer scale 2^-l is exact.
+ * A coordinate outside ]-1, w_l + 1[ (or NaN) is discarded before the
+ * integer conversion; nearbyintf rounds half to even.  Returns 1 and the
+ * pixel if the point lands inside layer l, else 0. */
+int orc_pixel(float u0, float v0, int l, int32_t w, int32_t h, int32_t* pu, int32_t* pv) {
+    int32_t wl = w >> l, hl = h >> l;
+    float s = ldexpf(1.0f, -l);
+    float ul = u0 * s, vl = v0 * s;
+    if (!(ul > -1.0f && ul < (float)wl + 1.0f)) return 0;
+    if (!(vl > -1.0f && vl < (float)hl + 1.0f)) return 0;
+    int32_t iu = (int32_t)nearbyintf(ul);
+    int32_t iv = (int32_t)nearbyintf(vl);
+    if (iu < 0 || iu >= wl || iv < 0 || iv >= hl) return 0;
+    *pu = iu;
+    *pv = iv;
+    return 1;
+}
+
+static uint32_t f32_bits(float f) {
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+static float bits_f32(uint32_t b) {
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+static int64_t layer_offset(int32_t w, int32_t h, int l) {
+    int64_t off = 0;
+    for (int k = 0; k < l; ++k) off += (int64_t)(w >> k) * (int64_t)(h >> k);
+    return off;
+}
+
+/* Total pixels over all layers. */
+int64_t orc_pyramid_pixels(int32_t w, int32_t h, int levels) {
+    return layer_offset(w, h, levels);
+}
+
+/* ------------------------------------------------------------------ */
+/* Projection of all points, with the discard tests                     */
+/* ------------------------------------------------------------------ */
+
+/* For every point and layer: the pixel id (or -1 if discarded) and the FP32
+ * depth.  Tests in the order of Sec. 3.1: near plane (z must be a positive
+ * depth), normal culling (Eq. normalculling, optional), bounds (Eq.
+ * boundscheck).  The normal test is taken literally from the paper:
+ * keep iff (R n)^T (R x + t) / |R x + t| > 0; the positive norm does not
+ * change the sign, so it is evaluated as an FP32 dot product. */
+static void project_all(int64_t n, const float* xyz, const float* normals,
+                        const orc_intrinsics* K, const orc_pose* T, int levels, float znear,
+                        int32_t* pix, float* zf) {
+    for (int64_t i = 0; i < n; ++i) {
+        float X[3], u0, v0;
+        transform_f32(T, xyz + 3 * i, X);
+        camera_f32(K, X, &u0, &v0);
+        float z = X[2];
+        zf[i] = z;
+        int keep = (z > znear);
+        if (keep && normals) {
+            const float* nn = normals + 3 * i;
+            float Rn[3];
+            for (int r = 0; r < 3; ++r) {
+                float s = T->R[3 * r + 0] * nn[0];
+                s = s + T->R[3 * r + 1] * nn[1];
+                s = s + T->R[3 * r + 2] * nn[2];
+                Rn[r] = s;
+            }
+            float dot = Rn[0] * X[0];
+            dot = dot + Rn[1] * X[1];
+            dot = dot + Rn[2] * X[2];
+            keep = (dot > 0.0f);
+        }
+        for (int l = 0; l < levels; ++l) {
+            int32_t pu, pv;
+            if (keep && orc_pixel(u0, v0, l, K->w, K->h, &pu, &pv))
+                pix[i * levels + l] = pv * (K->w >> l) + pu;
+            else
+                pix[i * levels + l] = -1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward (Eq. render, Eq. depthtest, Eq. blend)                       */
+/* ------------------------------------------------------------------ */
+
+/*
+ * orc_forward: one camera.
+ *   feat       n x c, double
+ *   background c doubles or NULL (= 0): the value of an empty pixel.  The
+ *              paper samples an environment map there; a constant stands in.
+ * Outputs (all over the concatenated pyramid of `levels` layers):
+ *   keys  uint64 per pixel; cnt  |Lambda| per pixel; img  c x h_l x w_l;
+ *   pix   n x levels pixel id or -1 (may be NULL); zf  n depths (may be NULL).
+ * Returns 0, or -1 if an allocation fails.
+ */
+int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, const float* normals,
+                const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
+                float znear, const double* background,
+                uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out) {
+    int64_t npx = orc_pyramid_pixels(K->w, K->h, levels);
+    int32_t* pix = pix_out ? pix_out : (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * levels + 1));
+    float* zf = z_out ? z_out : (float*)malloc(sizeof(float) * (size_t)(n + 1));
+    double* sum = (double*)calloc((size_t)(npx * c + 1), sizeof(double));
+    if (!pix || !zf || !sum) return -1;
+
+    /* Step 1: project every point to every layer (Eqs. projection, round,
+     * boundscheck, normalculling). */
+    project_all(n, xyz, normals, K, T, levels, znear, pix, zf);
+
+    /* Step 2: nearest depth per pixel, as a (depth bits, index) key so that
+     * equal depths resolve to the smallest point index. */
+    for (int64_t p = 0; p < npx; ++p) keys[p] = UINT64_MAX;
+    for (int l = 0; l < levels; ++l) {
+        int64_t off = layer_offset(K->w, K->h, l);
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t p = pix[i * levels + l];
+            if (p < 0) continue;
+            uint64_t key = ((uint64_t)f32_bits(zf[i]) << 32) | (uint64_t)(uint32_t)i;
+            if (key < keys[off + p]) keys[off + p] = key;
+        }
+    }
+
+    /* Step 3: fuzzy depth test (Eq. depthtest) against min_z(p), taken in
+     * FP32: pass iff z <= f32(min_z * f32(1 + alpha)).  Step 4: Lambda's
+     * size and the feature sum, for the mean of Eq. blend. */
+    const float a1 = 1.0f + alpha;
+    for (int64_t p = 0; p < npx; ++p) cnt[p] = 0;
+    for (int l = 0; l < levels; ++l) {
+        int64_t off = layer_offset(K->w, K->h, l);
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t p = pix[i * levels + l];
+            if (p < 0) continue;
+            float minz = bits_f32((uint32_t)(keys[off + p] >> 32));
+            float thr = minz * a1;
+            if (!(zf[i] <= thr)) continue;
+            cnt[off + p] += 1;
+            for (int ch = 0; ch < c; ++ch) sum[(off + p) * c + ch] += feat[i * c + ch];
+        }
+    }
+
+    /* Step 5: Eq. blend -- the mean over Lambda, or the background. */
+    for (int l = 0; l < levels; ++l) {
+        int64_t off = layer_offset(K->w, K->h, l);
+        int64_t np = (int64_t)(K->w >> l) * (K->h >> l);
+        for (int64_t p = 0; p < np; ++p) {
+            for (int ch = 0; ch < c; ++ch) {
+                double v;
+                if (cnt[off + p] == 0)
+                    v = background ? background[ch] : 0.0;
+                else
+                    v = sum[(off + p) * c + ch] / (double)cnt[off + p];
+                img[c * off + (int64_t)ch * np + p] = v;
+            }
+        }
+    }
+    free(sum);
+    if (!pix_out) free(pix);
+    if (!z_out) free(zf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 projection and its Jacobians (chain rule, Eq. partial)          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * For the chain rule the continuous projection is re-evaluated in FP64 from
+ * the same FP32 inputs.  Outputs:
+ *   uv[2]      (u0, v0)
+ *   X[3]       camera-space point
+ *   J_X[6]     d(u0,v0)/dX, row-major 2 x 3
+ *   J_K[12]    d(u0,v0)/d(fx, fy, cx, cy, k1, k2), row-major 2 x 6
+ */
+/* The camera model C in FP64 with FP64 parameters k9 = (fx, fy, cx, cy, k1,
+ * k2, k3, p1, p2), for a camera-space point X.  Exported for the
+ * finite-difference pins (intrinsics and pose perturbed in FP64). */
+void orc_camera_f64(const double* k9, const double* X, double* uv) {
+    const double fx = k9[0], fy = k9[1], cx = k9[2], cy = k9[3];
+    const double k1 = k9[4], k2 = k9[5], k3 = k9[6], p1 = k9[7], p2 = k9[8];
+    const double xn = X[0] / X[2], yn = X[1] / X[2];
+    const double r2 = xn * xn + yn * yn;
+    const double d = 1.0 + k1 * r2 + k2 * r2 * r2 + k3 * r2 * r2 * r2;
+    const double xd = xn * d + 2.0 * p1 * xn * yn + p2 * (r2 + 2.0 * xn * xn);
+    const double yd = yn * d + p1 * (r2 + 2.0 * yn * yn) + 2.0 * p2 * xn * yn;
+    uv[0] = fx * xd + cx;
+    uv[1] = fy * yd + cy;
+}
+
+/* orc_camera_f64 over n camera-space points (X: n x 3, uv: n x 2). */
+void orc_camera_f64_many(int64_t n, const double* k9, const double* X, double* uv) {
+    for (int64_t i = 0; i < n; ++i) orc_camera_f64(k9, X + 3 * i, uv + 2 * i);
+}
+
+void orc_project_jac_f64(const orc_intrinsics* K, const orc_pose* T, const float* x,
+                         double* uv, double* X, double* J_X, double* J_K) {
+    for (int r = 0; r < 3; ++r) {
+        X[r] = (double)T->R[3 * r + 0] * x[0] + (double)T->R[3 * r + 1] * x[1] +
+               (double)T->R[3 * r + 2] * x[2] + (double)T->t[r];
+    }
+    const double k9[9] = {K->fx, K->fy, K->cx, K->cy, K->k1, K->k2, K->k3, K->p1, K->p2};
+    orc_camera_f64(k9, X, uv);
+    const double fx = K->fx, fy = K->fy;
+    const double k1 = K->k1, k2 = K->k2, k3 = K->k3, p1 = K->p1, p2 = K->p2;
+    const double xn = X[0] / X[2], yn = X[1] / X[2];
+    const double r2 = xn * xn + yn * yn;
+    const double d = 1.0 + k1 * r2 + k2 * r2 * r2 + k3 * r2 * r2 * r2;
+    const double dd_dr2 = k1 + 2.0 * k2 * r2 + 3.0 * k3 * r2 * r2;
+    const double xd = xn * d + 2.0 * p1 * xn * yn + p2 * (r2 + 2.0 * xn * xn);
+    const double yd = yn * d + p1 * (r2 + 2.0 * yn * yn) + 2.0 * p2 * xn * yn;
+
+    /* d(xd, yd)/d(xn, yn) */
+    const double dxd_dxn = d + xn * dd_dr2 * 2.0 * xn + 2.0 * p1 * yn + p2 * 6.0 * xn;
+    const double dxd_dyn = xn * dd_dr2 * 2.0 * yn + 2.0 * p1 * xn + p2 * 2.0 * yn;
+    const double dyd_dxn = yn * dd_dr2 * 2.0 * xn + p1 * 2.0 * xn + 2.0 * p2 * yn;
+    const double dyd_dyn = d + yn * dd_dr2 * 2.0 * yn + p1 * 6.0 * yn + 2.0 * p2 * xn;
+    /* d(xn, yn)/dX */
+    const double iz = 1.0 / X[2];
+    const double dxn_dX[3] = {iz, 0.0, -X[0] * iz * iz};
+    const double dyn_dX[3] = {0.0, iz, -X[1] * iz * iz};
+    for (int k = 0; k < 3; ++k) {
+        J_X[k] = fx * (dxd_dxn * dxn_dX[k] + dxd_dyn * dyn_dX[k]);
+        J_X[3 + k] = fy * (dyd_dxn * dxn_dX[k] + dyd_dyn * dyn_dX[k]);
+    }
+    /* intrinsics: fx, fy, cx, cy, k1, k2 */
+    J_K[0] = xd;  J_K[1] = 0.0; J_K[2] = 1.0; J_K[3] = 0.0;
+    J_K[4] = fx * xn * r2;  J_K[5] = fx * xn * r2 * r2;
+    J_K[6] = 0.0; J_K[7] = yd;  J_K[8] = 0.0; J_K[9] = 1.0;
+    J_K[10] = fy * yn * r2; J_K[11] = fy * yn * r2 * r2;
+}
+
+/* ------------------------------------------------------------------ */
+/* Backward (Eqs. induce, gradp, spatialderiv; chain rule Eq. partial)  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * orc_backward: one camera, after orc_forward.
+ * Inputs: the forward's keys, cnt, img (FP64), pix, zf; the upstream
+ * gradient G = dL/dI over the pyramid (same layout as img).
+ * all_projected = 0: spatial gradients only for points in Lambda of their own
+ *   pixel (the point "projected at p" that is shown there); 1: for every
+ *   point that lands inside the layer.
+ * Outputs (overwritten, FP64):
+ *   dfeat n x c    dL/dtau: sum over layers of [i in Lambda] G(p)/|Lambda(p)|
+ *   dxyz  n x 3    dL/dx
+ *   dpose 6        dL/dxi for the left increment exp(xi)(R,t), xi = (nu, omega)
+ *   dintr 6        dL/d(fx, fy, cx, cy, k1, k2)
+ *   dpose_abs, dintr_abs  sum of |per (point, layer) term| (error scale)
+ *   gu, gv  n x levels   the layer-pixel gradients g_u, g_v (may be NULL)
+ *
+ * Induced change D at a target pixel q one pixel away (Eq. spatialderiv,
+ * read with the conditions on the target q):
+ *   q outside the layer                     -> 0
+ *   Lambda(q) empty                         -> tau - I(q)   (I(q) = background)
+ *   z > f32(min_z(q) (1+alpha))             -> 0            (behind)
+ *   f32(z (1+alpha)) < min_z(q)             -> tau - I(q)   (in front)
+ *   otherwise (fuzzy-equal)                 -> (|Lambda| I(q) + tau)/(1+|Lambda|) - I(q)
+ * Eq. gradp with the shift to u-1 having du = -1, contracted with G at the
+ * target:  g_u = 1/2 ( <G(u+1,v), D(u+1,v)> - <G(u-1,v), D(u-1,v)> ), and
+ * likewise g_v from (u, v+-1).  g is in layer pixels; the layer scale 2^-l
+ * maps it to layer-0 pixels.
+ */
+int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
+                 const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
+                 const double* background, int32_t all_projected,
+                 const uint64_t* keys, const uint32_t* cnt, const double* img,
+                 const int32_t* pix, const float* zf, const double* G,
+                 double* dfeat, double* dxyz, double* dpose, double* dintr,
+                 double* dpose_abs, double* dintr_abs, double* gu_out, double* gv_out) {
+    const float a1 = 1.0f + alpha;
+    double* D = (double*)malloc(sizeof(double) * (size_t)(c > 0 ? c : 1));
+    if (!D) return -1;
+    for (int k = 0; k < 6; ++k) dpose[k] = dintr[k] = dpose_abs[k] = dintr_abs[k] = 0.0;
+    for (int64_t i = 0; i < n * c; ++i) dfeat[i] = 0.0;
+    for (int64_t i = 0; i < n * 3; ++i) dxyz[i] = 0.0;
+    if (gu_out)
+        for (int64_t i = 0; i < n * levels; ++i) gu_out[i] = gv_out[i] = 0.0;
+
+    for (int64_t i = 0; i < n; ++i) {
+        const double* tau = feat + i * c;
+        double dL_du0 = 0.0, dL_dv0 = 0.0;
+        double tu[8], tv[8]; /* per layer contributions to du0, dv0 */
+        for (int l = 0; l < levels; ++l) {
+            tu[l] = tv[l] = 0.0;
+            int32_t p = pix[i * levels + l];
+            if (p < 0) continue;
+            const int32_t wl = K->w >> l, hl = K->h >> l;
+            const int64_t np = (int64_t)wl * hl;
+            const int64_t off = layer_offset(K->w, K->h, l);
+            const double* Il = img + c * off;
+            const double* Gl = G + c * off;
+            float minz_p = bits_f32((uint32_t)(keys[off + p] >> 32));
+            int in_lambda = (zf[i] <= minz_p * a1);
+
+            /* Feature gradient: d mean / d tau_i = 1/|Lambda| for members. */
+            if (in_lambda)
+                for (int ch = 0; ch < c; ++ch)
+                    dfeat[i * c + ch] += Gl[(int64_t)ch * np + p] / (double)cnt[off + p];
+
+            if (!in_lambda && !all_projected) continue;
+            const int32_t pu = p % wl, pv = p / wl;
+            const int32_t du[4] = {+1, -1, 0, 0};
+            const int32_t dv[4] = {0, 0, +1, -1};
+            double contrib[4];
+            for (int s = 0; s < 4; ++s) {
+                contrib[s] = 0.0;
+                int32_t qu = pu + du[s], qv = pv + dv[s];
+                if (qu < 0 || qu >= wl || qv < 0 || qv >= hl) continue;
+                int64_t q = (int64_t)qv * wl + qu;
+                uint32_t nq = cnt[off + q];
+                float minz_q = bits_f32((uint32_t)(keys[off + q] >> 32));
+                for (int ch = 0; ch < c; ++ch) {
+                    double Iq = Il[(int64_t)ch * np + q];
+                    if (nq == 0)
+                        D[ch] = tau[ch] - Iq; /* background overwritten */
+                    else if (zf[i] > minz_q * a1)
+                        D[ch] = 0.0; /* behind the target's surface */
+                    else if (zf[i] * a1 < minz_q)
+                        D[ch] = tau[ch] - Iq; /* in front: replaces the mean */
+                    else
+                        D[ch] = ((double)nq * Iq + tau[ch]) / (1.0 + (double)nq) - Iq;
+                }
+                double dot = 0.0;
+                for (int ch = 0; ch < c; ++ch) dot += Gl[(int64_t)ch * np + q] * D[ch];
+                contrib[s] = dot;
+            }
+            double g_u = 0.5 * (contrib[0] - contrib[1]);
+            double g_v = 0.5 * (contrib[2] - contrib[3]);
+            if (gu_out) {
+                gu_out[i * levels + l] = g_u;
+                gv_out[i * levels + l] = g_v;
+            }
+            double sc = ldexp(1.0, -l);
+            tu[l] = g_u * sc;
+            tv[l] = g_v * sc;
+            dL_du0 += tu[l];
+            dL_dv0 += tv[l];
+        }
+        if (dL_du0 == 0.0 && dL_dv0 == 0.0) {
+            int any = 0;
+            for (int l = 0; l < levels; ++l) any |= (tu[l] != 0.0 || tv[l] != 0.0);
+            if (!any) continue;
+        }
+        double uv[2], X[3], J_X[6], J_K[12];
+        orc_project_jac_f64(K, T, xyz + 3 * i, uv, X, J_X, J_K);
+        double dX[3];
+        for (int k = 0; k < 3; ++k) dX[k] = J_X[k] * dL_du0 + J_X[3 + k] * dL_dv0;
+        /* dL/dx = R^T dL/dX */
+        for (int k = 0; k < 3; ++k)
+            dxyz[i * 3 + k] = (double)T->R[0 * 3 + k] * dX[0] + (double)T->R[1 * 3 + k] * dX[1] +
+                              (double)T->R[2 * 3 + k] * dX[2];
+        /* Left increment exp(xi)(R,t): X' = X + nu + omega x X, so
+         * dL/dnu = dL/dX and dL/domega = X x dL/dX. */
+        double dxi[6] = {dX[0], dX[1], dX[2],
+                         X[1] * dX[2] - X[2] * dX[1],
+                         X[2] * dX[0] - X[0] * dX[2],
+                         X[0] * dX[1] - X[1] * dX[0]};
+        for (int k = 0; k < 6; ++k) {
+            dpose[k] += dxi[k];
+            double dk = J_K[k] * dL_du0 + J_K[6 + k] * dL_dv0;
+            dintr[k] += dk;
+        }
+        /* error scale: sum of the magnitudes of each layer's own term */
+        for (int l = 0; l < levels; ++l) {
+            if (tu[l] == 0.0 && tv[l] == 0.0) continue;
+            double eX[3];
+            for (int k = 0; k < 3; ++k) eX[k] = J_X[k] * tu[l] + J_X[3 + k] * tv[l];
+            double exi[6] = {eX[0], eX[1], eX[2],
+                             X[1] * eX[2] - X[2] * eX[1],
+                             X[2] * eX[0] - X[0] * eX[2],
+                             X[0] * eX[1] - X[1] * eX[0]};
+            for (int k = 0; k < 6; ++k) {
+                dpose_abs[k] += fabs(exi[k]);
+                dintr_abs[k] += fabs(J_K[k] * tu[l] + J_K[6 + k] * tv[l]);
+            }
+        }
+    }
+    free(D);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Photometric epilogue on layer 0 (Sec. 3.3)                           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * In-place on the layer-0 planes of img (c x h x w), channels 0..min(c,3)-1:
+ *   I_e = I / 2^EV                         (exposure)
+ *   I_w = I_e * wb[ch]                     (white balance, multiplicative)
+ *   I_v = I_w * (1 + a2 r^2 + a4 r^4 + a6 r^6),
+ *         r = |(u/w, v/h) - c_v|           (vignette, normalised coords)
+ *   out = R_ch(I_v)                        (response curve: LUT of crf_n
+ *         samples on [0,1], linear interpolation, input clamped to [0,1])
+ * If crf_n < 2 the response curve is the identity (no clamp).
+ * If grad is not NULL it receives d out / d I per element (same layout), for
+ * chaining an upstream gradient through the epilogue.
+ */
+void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const double* wb,
+                  const double* vig_c, const double* vig_a, const double* crf_lut, int32_t crf_n,
+                  double* grad) {
+    const int64_t np = (int64_t)w * h;
+    const int cc = c < 3 ? c : 3;
+    const double e = pow(2.0, -ev);
+    for (int ch = 0; ch < cc; ++ch) {
+        for (int32_t v = 0; v < h; ++v) {
+            for (int32_t u = 0; u < w; ++u) {
+                int64_t p = (int64_t)v * w + u;
+                double ru = (double)u / w - vig_c[0];
+                double rv = (double)v / h - vig_c[1];
+                double r2 = ru * ru + rv * rv;
+                double vig = 1.0 + vig_a[0] * r2 + vig_a[1] * r2 * r2 + vig_a[2] * r2 * r2 * r2;
+                double scale = e * wb[ch] * vig;
+                double x = img[(int64_t)ch * np + p] * scale;
+                double y = x, dy = 1.0;
+                if (crf_n >= 2) {
+                    const double* lut = crf_lut + (int64_t)ch * crf_n;
+                    double xc = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+                    double pos = xc * (crf_n - 1);
+                    int32_t i0 = (int32_t)floor(pos);
+                    if (i0 > crf_n - 2) i0 = crf_n - 2;
+                    double f = pos - i0;
+                    y = lut[i0] * (1.0 - f) + lut[i0 + 1] * f;
+                    dy = (x < 0.0 || x > 1.0) ? 0.0 : (lut[i0 + 1] - lut[i0]) * (crf_n - 1);
+                }
+                img[(int64_t)ch * np + p] = y;
+                if (grad) grad[(int64_t)ch * np + p] = dy * scale;
+            }
+        }
+    }
+    if (grad)
+        for (int ch = cc; ch < c; ++ch)
+            for (int64_t p = 0; p < np; ++p) grad[(int64_t)ch * np + p] = 1.0;
+}
