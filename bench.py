@@ -1,0 +1,472 @@
+#!/usr/bin/env python
+"""Throughput of ADOP's differentiable one-pixel point rasterizer (forward +
+backward) on one camera view at 1920x1080.
+
+Workload (default): 5,000,000 points on 25 planes and 25 spheres in a 10 m box
+(depth complexity ~8), 8 descriptor channels stored in BF16 (FP32 measured
+beside it), a distorted pinhole camera (fx = fy = 1500, k1 = -0.05, k2 = 0.01)
+12 m from the centre, 4 pyramid layers, fuzzy threshold alpha = 0.01; forward
+plus backward to descriptors, positions, the 6-DoF pose and intrinsics.  One
+step = one forward + one backward of that view through the C ABI.
+
+Metric: points/s (points processed through all 4 layers of one camera,
+forward + backward) -- higher is better.  The JSON line also carries the
+roofline of the dominant kernel, the FP32 comparison, an end-to-end number
+with host buffers, the clock record and the CPU oracle's rate.
+
+--impl reference times the CPU oracle (the plain FP64 statement of the
+method) on the same workload, a bounded sample of points per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "points/sec fwd+bwd at 1920x1080 (BF16 vs FP32, % HBM roofline); served p50/p99 ms"
+UNIT = "points/s"
+L2_FLUSH_BYTES = 256 << 20
+LEVELS = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--points", type=int, default=5_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="a few steps, no extras (for ncu)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data exchange)
+# ---------------------------------------------------------------------------
+
+def dist_setup(backend=None):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    if backend is None:
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    return dist, dist.get_rank(), dist.get_world_size()
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(step, k: int, flush=None, dist=None, device="cuda"):
+    """Time exactly k calls of step(): barrier + synchronize on both sides,
+    per-step CUDA events on the current stream (an optional L2 flush between
+    steps is outside the events).  Returns (total device ms, per-step ms)."""
+    import torch
+    cuda = str(device).startswith("cuda")
+    if dist is not None:
+        dist.barrier()
+    if cuda:
+        torch.cuda.synchronize()
+    times = []
+    if cuda:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            if flush is not None:
+                flush()
+            evs[i][0].record()
+            step()
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        times = [a.elapsed_time(b) for a, b in evs]
+    else:
+        for i in range(k):
+            if flush is not None:
+                flush()
+            t0 = time.perf_counter()
+            step()
+            times.append((time.perf_counter() - t0) * 1e3)
+    if dist is not None:
+        dist.barrier()
+    if cuda:
+        torch.cuda.synchronize()
+    return float(sum(times)), times
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: int) -> int:
+    """Compulsory HBM bytes of one launch: every input read once, every output
+    written once (per camera; n points, px pyramid pixels, c channels)."""
+    rs = ((c + 3) + 3) // 4 * 4
+    return {
+        "clear": px * (8 + 4 + 4 * c),                          # write key, count, sums
+        "depth": n * 12 + px * 8 * 2,                           # read xyz; read+write keys
+        "accumulate": n * (12 + c * s_feat) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau; keys; RMW count+sums
+        "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
+        "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 4 * rs),   # key, count, sums, G -> records
+        "bwd_points": n * (12 + c * s_feat + 4 * c + 12) + px * 4 * rs,  # xyz, tau -> dtau, dx; records
+        "bwd_reduce": 0,
+    }[kernel]
+
+
+class Workload:
+    def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None):
+        import torch
+        import paper_2110_06635_gb300 as adop
+        import scenes
+        self.adop = adop
+        if scene is None:
+            scene, cams = scenes.config(2, n=n_points)
+            cam = cams[0]
+        self.scene, self.cam = scene, cam
+        self.n, self.c = scene.n, scene.c
+        self.device = device
+        self.feat_dtype = feat_dtype
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[feat_dtype]
+        self.xyz = torch.from_numpy(scene.xyz).to(device)
+        if feat_dtype == "bf16":
+            self.feat = torch.from_numpy(scene.feat_as("bf16").view(np.int16)).to(device).view(torch.bfloat16)
+        else:
+            self.feat = torch.from_numpy(scene.feat).to(device)
+        self.out_dtype = tdt
+        self.pts = adop.Points(self.xyz, self.feat)
+        self.params = adop.Params(LEVELS, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+        self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device)
+        self.ws = adop.alloc_workspace(self.pts, [cam], self.params, None, device)
+        G = scenes.upstream_grad(cam.w, cam.h, LEVELS, self.c, 2024)
+        self.G_host = G
+        self.G = [torch.from_numpy(g).to(device) for g in G]
+        self.gfeat = torch.empty((self.n, self.c), dtype=torch.float32, device=device)
+        self.gxyz = torch.empty((self.n, 3), dtype=torch.float32, device=device)
+        self.gpose = torch.zeros((1, 6), dtype=torch.float32, device=device)
+        self.gintr = torch.zeros((1, 6), dtype=torch.float32, device=device)
+        self.px = adop.pyramid_offsets(cam.w, cam.h, LEVELS)[-1]
+        self.s_feat = 2 if feat_dtype == "bf16" else 4
+        self._prepare()
+
+    def _prepare(self):
+        """Marshal the C structs once, so a step is two foreign calls."""
+        import ctypes as ct
+        from paper_2110_06635_gb300 import _abi as A
+        lib = A.load()
+        self._lib = lib
+        self._ps = self.pts.struct()
+        self._pr = self.params.struct()
+        self._cams = A._cams_array([self.cam])
+        self._fr = (A.adop_frame * 1)(self.frame.struct())
+        self._g = (ct.c_void_p * LEVELS)(*[g.data_ptr() for g in self.G])
+        self._wp, self._wn = A._ws_ptr(self.ws)
+        self._ct = ct
+
+    def step(self, stream_ptr):
+        ct = self._ct
+        st = self._lib.adop_render_forward(ct.byref(self._ps), self._cams, 1, ct.byref(self._pr), self._fr,
+                                           self._wp, self._wn, stream_ptr)
+        if st != 0:
+            raise RuntimeError(self._lib.adop_last_error().decode())
+        st = self._lib.adop_render_backward(ct.byref(self._ps), self._cams, 1, ct.byref(self._pr), self._fr,
+                                            self._g, self.gfeat.data_ptr(), self.gxyz.data_ptr(),
+                                            self.gpose.data_ptr(), self.gintr.data_ptr(), self._wp, self._wn,
+                                            stream_ptr)
+        if st != 0:
+            raise RuntimeError(self._lib.adop_last_error().decode())
+
+
+def run_ours(args, dist, rank, world):
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    adop.build()
+    adop.load()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        flush_buf.zero_()
+
+    stream = torch.cuda.current_stream()
+    sp = ct.c_void_p(stream.cuda_stream)
+    results = {}
+    dtypes = ["bf16"] if (args.no_fp32 or args.profile_only) else ["bf16", "f32"]
+    clocks = None
+    for dt in dtypes:
+        wl = Workload(args.points, dt, device)
+        for _ in range(args.warmup):
+            wl.step(sp)
+        torch.cuda.synchronize()
+        adop.adop_profile_enable(True)
+        adop.adop_profile_collect()
+        gpu_uuid = str(torch.cuda.get_device_properties(device).uuid)
+        sampler = ClockSampler(gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}")
+        with sampler:
+            total_ms, per = timed_steps(lambda: wl.step(sp), args.steps, flush, dist, device)
+        kstats = adop.adop_profile_collect()
+        adop.adop_profile_enable(False)
+        if dt == "bf16":
+            clocks = sampler.summary()
+        tmax = max_over_ranks(dist, total_ms, device)
+        results[dt] = {"wl": wl, "total_ms": tmax, "per": per, "kstats": kstats}
+        if dt != dtypes[-1]:
+            del wl
+            torch.cuda.empty_cache()
+    return results, clocks, device
+
+
+def e2e_measure(wl, steps: int, warmup: int, device):
+    """Same step through the public API, from and to pinned host memory:
+    H2D of positions, descriptors and upstream gradients, D2H of the images
+    and all gradients, inside the timed region."""
+    import ctypes as ct
+    import torch
+    pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)  # noqa: E731
+    h_in = [(pin(t), t) for t in (wl.xyz, wl.feat, *wl.G)]
+    for h, d in h_in:
+        h.copy_(d.cpu())
+    outs = [*wl.frame.images, wl.gfeat, wl.gxyz, wl.gpose, wl.gintr]
+    h_out = [(pin(t), t) for t in outs]
+    stream = torch.cuda.current_stream()
+    sp = ct.c_void_p(stream.cuda_stream)
+
+    def step():
+        for h, d in h_in:
+            d.copy_(h, non_blocking=True)
+        wl.step(sp)
+        for h, d in h_out:
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    total_ms, _ = timed_steps(step, steps, None, None, device)
+    bi = sum(h.numel() * h.element_size() for h, _ in h_in)
+    bo = sum(h.numel() * h.element_size() for h, _ in h_out)
+    return total_ms, bi, bo
+
+
+def cpu_baseline(budget_s: float = 15.0):
+    """The oracle as it stands on the host, single thread, on a bounded
+    sample of the workload's points (same camera, full 1080p pyramid)."""
+    import oracle
+    import scenes
+    sc, cams = scenes.config(2)
+    cam = cams[0]
+    feat = sc.feat_as("bf16")
+    G = scenes.upstream_grad(cam.w, cam.h, LEVELS, sc.c, 2024)
+    Gf = np.concatenate([g.ravel() for g in G]).astype(np.float64)
+    rng = np.random.default_rng(99)
+    m = 500_000
+    done, t_used, reps = 0, 0.0, 0
+    while t_used < budget_s and reps < 64:
+        idx = np.sort(rng.choice(sc.n, size=min(m, sc.n), replace=False))
+        xyz, fe = sc.xyz[idx], feat[idx]
+        t0 = time.perf_counter()
+        f = oracle.forward(xyz, fe, cam, LEVELS, 0.01, 1e-3)
+        oracle.backward(f, xyz, fe, cam, Gf, 0.01)
+        t_used += time.perf_counter() - t0
+        done += len(idx)
+        reps += 1
+    return {"value": done / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x {m} points drawn from the 5M-point workload, full 1920x1080 4-layer pyramid, "
+                      f"fwd+bwd, FP64 C oracle, single thread, {t_used:.1f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return main_reference(args)
+    dist, rank, world = dist_setup()
+    results, clocks, device = run_ours(args, dist, rank, world)
+    bf = results["bf16"]
+    wl = bf["wl"]
+    K = args.steps
+    ms_per_step = bf["total_ms"] / K
+    value = world * wl.n * K / (bf["total_ms"] / 1e3)
+    peak, peak_kind = measured_peaks()
+    # dominant kernel by device time
+    ks = bf["kstats"]
+    dom = max(ks, key=lambda k: ks[k][1])
+    launches, dom_ms = ks[dom]
+    ab = algorithmic_bytes(dom, wl.n, wl.px, wl.c, wl.s_feat, 2)
+    achieved = ab / (dom_ms / launches * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback", "traffic": None,
+                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": round(dom_ms / launches, 4)}
+    kernel_ms = {k: round(v[1] / v[0], 4) for k, v in ks.items()}
+    step_bytes = sum(algorithmic_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, 2) for k in ks)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 storage, f32 arithmetic", "data": "synthetic",
+        "config": {"workload": "single view 1920x1080: 5M points on 50 seeded surfaces (depth complexity ~8), "
+                               "C=8 BF16 descriptors, 4 layers, alpha=0.01, fwd+bwd to tau, x, pose, intrinsics",
+                   "points": wl.n, "resolution": "1920x1080", "channels": wl.c, "levels": LEVELS,
+                   "feat_dtype": "bf16", "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "kernel_ms": kernel_ms,
+        "step_hbm_fraction": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+        "gpu_launches": int(sum(v[0] for v in ks.values())),
+        "clocks": clocks,
+    }
+    if "f32" in results:
+        f32 = results["f32"]
+        line["fp32"] = {"value": round(world * f32["wl"].n * K / (f32["total_ms"] / 1e3), 1),
+                        "ms_per_step": round(f32["total_ms"] / K, 4),
+                        "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in f32["kstats"].items()}}
+    if not args.no_e2e and not args.profile_only:
+        e2e_ms, bi, bo = e2e_measure(wl, max(3, K // 2), 2, device)
+        ksteps = max(3, K // 2)
+        e2e_ms = max_over_ranks(dist, e2e_ms, device)
+        line["e2e"] = {"value": round(world * wl.n * ksteps / (e2e_ms / 1e3), 1), "unit": UNIT,
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    """The oracle timed on the host cores: each step is a bounded sample of
+    the same workload (points drawn from the 5M-point cloud, full pyramid)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import scenes
+    sc, cams = scenes.config(2)
+    cam = cams[0]
+    feat = sc.feat_as("bf16")
+    G = scenes.upstream_grad(cam.w, cam.h, LEVELS, sc.c, 2024)
+    Gf = np.concatenate([g.ravel() for g in G]).astype(np.float64)
+    rng = np.random.default_rng(7)
+    # size each step so the whole run stays within about two minutes
+    per_step_s = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    probe = np.sort(rng.choice(sc.n, 100_000, replace=False))
+    t0 = time.perf_counter()
+    f = oracle.forward(sc.xyz[probe], feat[probe], cam, LEVELS, 0.01, 1e-3)
+    oracle.backward(f, sc.xyz[probe], feat[probe], cam, Gf, 0.01)
+    t_probe = time.perf_counter() - t0
+    m = int(min(sc.n, max(10_000, 100_000 * per_step_s / max(t_probe, 1e-3))))
+
+    def step():
+        idx = np.sort(rng.choice(sc.n, m, replace=False))
+        fw = oracle.forward(sc.xyz[idx], feat[idx], cam, LEVELS, 0.01, 1e-3)
+        oracle.backward(fw, sc.xyz[idx], feat[idx], cam, Gf, 0.01)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (bf16 descriptors upcast)", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "single view 1920x1080: 5M points on 50 seeded surfaces, C=8 BF16, 4 layers, "
+                                   "fwd+bwd; each step a sample of the cloud", "points_per_step": m},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{m} points per step drawn from the 5M-point cloud, full 1080p pyramid"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * adop.h -- C ABI of a GB300 (sm_103a) implementation of ADOP's
+ * differentiable one-pixel point rasterizer.
+ *
+ * Paper: D. Rueckert, L. Franke, M. Stamminger, "ADOP: Approximate
+ * Differentiable One-Pixel Point Rendering" (arXiv 2110.06635), Sec. 3.1
+ * (rasterizer, forward and backward), Sec. 3.3 (photometric camera model).
+ *
+ * Conventions shared by every call
+ *   - All array arguments are DEVICE pointers owned by the caller (for
+ *     example memory allocated by PyTorch), except the structs themselves,
+ *     which are read on the host during the call and may be freed when it
+ *     returns.  The library allocates no device memory in these calls.
+ *   - Calls are asynchronous on the given CUDA stream (`adop_stream` is
+ *     ABI-compatible with cudaStream_t; NULL = the legacy default stream).
+ *     Argument errors are detected on the host, before anything is
+ *     launched, and returned synchronously.  A launch failure returns
+ *     ADOP_ERR_CUDA.  No call aborts or traps.
+ *   - adop_last_error() returns a thread-local description of the last
+ *     non-OK status returned on the calling thread.
+ *   - Layer l of the image pyramid has w_l = w >> l, h_l = h >> l pixels;
+ *     pixel (pu, pv) of layer l has id pv * w_l + pu.
+ */
+#ifndef ADOP_H
+#define ADOP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADOP_MAX_LEVELS 8          /* pyramid layers per camera (the paper uses 4) */
+#define ADOP_MAX_CAMERAS 64        /* cameras per call */
+#define ADOP_ABI_VERSION 1
+
+struct CUstream_st;
+typedef struct CUstream_st* adop_stream; /* == cudaStream_t */
+
+typedef enum {
+    ADOP_OK = 0,
+    ADOP_ERR_INVALID_ARG = 1,  /* a pointer, size, shape or flag is invalid */
+    ADOP_ERR_UNSUPPORTED = 2,  /* valid, but not implemented (e.g. channel count) */
+    ADOP_ERR_OUT_OF_MEMORY = 3,/* workspace too small / server budget exhausted */
+    ADOP_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    ADOP_ERR_TIMEOUT = 5,      /* a bounded wait ran out */
+    ADOP_ERR_BUSY = 6,         /* not finished yet (polling) */
+    ADOP_ERR_CANCELLED = 7     /* the request was cancelled */
+} adop_status;
+
+typedef enum { ADOP_F32 = 0, ADOP_BF16 = 1, ADOP_F16 = 2 } adop_dtype;
+
+/* Camera model C of Eq. render: pinhole with Brown-Conrady distortion.
+ *   xn = X/Z, yn = Y/Z, r2 = xn^2 + yn^2, d = 1 + r2 (k1 + r2 (k2 + r2 k3))
+ *   xd = xn d + 2 p1 xn yn + p2 (r2 + 2 xn^2), yd = yn d + p1 (r2 + 2 yn^2) + 2 p2 xn yn
+ *   u0 = fx xd + cx, v0 = fy yd + cy, and layer l uses (u0, v0) / 2^l.
+ * w, h: layer-0 image size in pixels (1 .. 16384). */
+typedef struct {
+    int32_t w, h;
+    float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+} adop_intrinsics;
+
+/* World-to-camera rigid transform (R, t) of Eq. render; X = R x + t, R row-major. */
+typedef struct {
+    float R[9];
+    float t[3];
+} adop_pose;
+
+/* Per-image photometric model of Sec. 3.3, applied to channels 0..2 of
+ * layer 0 when enabled (and ADOP_FLAG_EPILOGUE is set):
+ *   I_e = I / 2^ev; I_w = I_e * wb[ch]; I_v = I_w (1 + a2 r^2 + a4 r^4 + a6 r^6)
+ *   with r = |(u / w, v / h) - vig_c|; out = R_ch(I_v), R_ch a piecewise-linear
+ *   LUT of crf_n samples on [0,1] (input clamped to [0,1]) at
+ *   crf_lut[ch * crf_n ...] (device pointer, 3 x crf_n floats), or the identity
+ *   if crf_lut is NULL. */
+typedef struct {
+    float ev;
+    float wb[3];
+    float vig_c[2];
+    float vig_a[3];
+    const float* crf_lut;
+    int32_t crf_n;
+    int32_t enabled;
+} adop_photometric;
+
+typedef struct {
+    adop_intrinsics K;
+    adop_pose T;
+    adop_photometric ph;
+} adop_camera;
+
+/* The point cloud: positions x (n x 3 FP32, 16-byte aligned), neural
+ * descriptors tau (n x c, feat_dtype, 16-byte aligned), optional normals
+ * (n x 3 FP32, used only with ADOP_FLAG_NORMAL_CULL).  c in {1,2,3,4,8,16};
+ * n < 2^31. */
+typedef struct {
+    int64_t n;
+    int32_t c;
+    adop_dtype feat_dtype;
+    const float* xyz;
+    const void* feat;
+    const float* normals;
+} adop_points;
+
+#define ADOP_FLAG_NORMAL_CULL (1u << 0)       /* Eq. normalculling; needs normals */
+#define ADOP_FLAG_GRAD_ALL_PROJECTED (1u << 1)/* spatial gradients also for occluded points */
+#define ADOP_FLAG_EPILOGUE (1u << 2)          /* apply the photometric model (fwd and bwd) */
+#define ADOP_FLAG_GRAD_ASSIGN (1u << 3)       /* grad_feat / grad_xyz are overwritten, not += */
+
+/* levels: pyramid layers L (1..ADOP_MAX_LEVELS); alpha: fuzzy depth-test
+ * threshold of Eq. depthtest (the paper uses 0.01); znear: points with
+ * depth z <= znear are discarded; background: c FP32 values (device) shown
+ * where no point lands (the paper's environment map), NULL = zeros. */
+typedef struct {
+    int32_t levels;
+    float alpha;
+    float znear;
+    const float* background;
+    uint32_t flags;
+} adop_params;
+
+/* Per-camera frame.  image[l]: output, c x h_l x w_l planar in out_dtype
+ * (NULL = layer not written).  key[l] (uint64 per pixel: bits(z_min) << 32 |
+ * index of the nearest point; UINT64_MAX when empty), count[l] (|Lambda|
+ * per pixel) and acc (FP32 feature sums, pixel-major: pixel p of layer l at
+ * acc[(off_l + p) * c], off_l = sum_{k<l} w_k h_k) are the per-pixel state
+ * that the backward pass re-uses.  Either all of key/count/acc are given
+ * (the forward fills them; the backward reads them) or all are NULL (the
+ * forward keeps them in the workspace; the backward re-renders them there,
+ * as the paper's backward pass does). */
+typedef struct {
+    void* image[ADOP_MAX_LEVELS];
+    uint64_t* key[ADOP_MAX_LEVELS];
+    uint32_t* count[ADOP_MAX_LEVELS];
+    float* acc;
+    adop_dtype out_dtype;
+} adop_frame;
+
+/* Bytes of device workspace that forward/backward need for these arguments
+ * (256-byte aligned pointer required).  Returns 0 on invalid arguments. */
+size_t adop_workspace_bytes(const adop_points* pts, const adop_camera* cams, int32_t n_cam,
+                            const adop_params* params);
+
+/*
+ * Forward pass, Sec. 3.1 (Eqs. render, round, boundscheck, normalculling,
+ * depthtest, blend): for every camera and layer, project every point,
+ * keep the nearest depth per pixel (packed 64-bit (depth, index) key, ties
+ * to the smallest index), blend the mean descriptor of all points within
+ * the fuzzy threshold z <= (1 + alpha) z_min, write background where no
+ * point lands, then the optional photometric epilogue (Sec. 3.3).
+ * The projection and depth are evaluated as a fixed sequence of FP32
+ * operations (no contraction), rounding ties to even; sums are FP32.
+ */
+adop_status adop_render_forward(const adop_points* pts, const adop_camera* cams, int32_t n_cam,
+                                const adop_params* params, adop_frame* frames, void* workspace,
+                                size_t workspace_bytes, adop_stream stream);
+
+/*
+ * Backward pass, Sec. 3.1 (Eqs. partial, induce, gradp, spatialderiv,
+ * tangent).  grad_image[k * levels + l]: dL/dI of camera k, layer l (FP32,
+ * c x h_l x w_l, NULL = zero).  Outputs (FP32, accumulated with += unless
+ * ADOP_FLAG_GRAD_ASSIGN):
+ *   grad_feat n x c   dL/dtau = sum over cameras/layers of G(p)/|Lambda(p)| for
+ *                     points in Lambda(p)
+ *   grad_xyz  n x 3   dL/dx from the one-pixel approximate spatial gradient
+ *                     (NULL = not computed)
+ *   grad_pose n_cam x 6  dL/dxi of the left increment exp(xi)(R,t), xi = (nu, omega)
+ *   grad_intr n_cam x 6  dL/d(fx, fy, cx, cy, k1, k2)
+ * (grad_pose / grad_intr always accumulate, NULL = not computed.)
+ * The induced change at a neighbour q of the point's pixel is: tau - I(q) if q
+ * is empty or the point is in front (z (1+alpha) < z_min(q)), 0 if it is
+ * behind (z > (1+alpha) z_min(q)), (tau - I(q)) / (1 + |Lambda(q)|) otherwise;
+ * g_u = (<G(u+1,v), D(u+1,v)> - <G(u-1,v), D(u-1,v)>) / 2, g_v likewise.
+ * frames: the forward's frames (key/count/acc NULL => re-rendered here).
+ */
+adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams, int32_t n_cam,
+                                 const adop_params* params, const adop_frame* frames,
+                                 const float* const* grad_image, float* grad_feat, float* grad_xyz,
+                                 float* grad_pose, float* grad_intr, void* workspace,
+                                 size_t workspace_bytes, adop_stream stream);
+
+/* Kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by a pair of CUDA events recorded on the launch's stream (a few
+ * microseconds of host time per launch, no device synchronisation).
+ * adop_profile_collect waits for the recorded events, adds each kernel's
+ * launches and device time into out[] (one entry per kernel name, at most
+ * max entries), clears the record and returns the number of entries
+ * (negative on a CUDA error).  Not part of the paper: instrumentation. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} adop_kernel_stat;
+
+adop_status adop_profile_enable(int32_t on);
+int32_t adop_profile_collect(adop_kernel_stat* out, int32_t max);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* adop_last_error(void);
+
+/* ADOP_ABI_VERSION of the loaded library. */
+int32_t adop_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADOP_H */

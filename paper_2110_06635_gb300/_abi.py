@@ -1,0 +1,321 @@
+"""Thin ctypes binding of ``include/adop.h``: the same entry points, with
+torch CUDA tensors in place of raw device pointers.  Argument marshalling
+only -- every step of the rasterizer runs in the CUDA library, and nothing
+here falls back to another implementation: if ``libadop.so`` is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _build
+
+ADOP_MAX_LEVELS = 8
+ADOP_MAX_CAMERAS = 64
+ADOP_FLAG_NORMAL_CULL = 1 << 0
+ADOP_FLAG_GRAD_ALL_PROJECTED = 1 << 1
+ADOP_FLAG_EPILOGUE = 1 << 2
+ADOP_FLAG_GRAD_ASSIGN = 1 << 3
+ADOP_F32, ADOP_BF16, ADOP_F16 = 0, 1, 2
+
+STATUS = {0: "ADOP_OK", 1: "ADOP_ERR_INVALID_ARG", 2: "ADOP_ERR_UNSUPPORTED", 3: "ADOP_ERR_OUT_OF_MEMORY",
+          4: "ADOP_ERR_CUDA", 5: "ADOP_ERR_TIMEOUT", 6: "ADOP_ERR_BUSY", 7: "ADOP_ERR_CANCELLED"}
+
+
+class AdopError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class adop_intrinsics(ct.Structure):
+    _fields_ = [("w", ct.c_int32), ("h", ct.c_int32)] + [
+        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")]
+
+
+class adop_pose(ct.Structure):
+    _fields_ = [("R", ct.c_float * 9), ("t", ct.c_float * 3)]
+
+
+class adop_photometric(ct.Structure):
+    _fields_ = [("ev", ct.c_float), ("wb", ct.c_float * 3), ("vig_c", ct.c_float * 2), ("vig_a", ct.c_float * 3),
+                ("crf_lut", ct.c_void_p), ("crf_n", ct.c_int32), ("enabled", ct.c_int32)]
+
+
+class adop_camera(ct.Structure):
+    _fields_ = [("K", adop_intrinsics), ("T", adop_pose), ("ph", adop_photometric)]
+
+
+class adop_points(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("c", ct.c_int32), ("feat_dtype", ct.c_int32), ("xyz", ct.c_void_p),
+                ("feat", ct.c_void_p), ("normals", ct.c_void_p)]
+
+
+class adop_params(ct.Structure):
+    _fields_ = [("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float), ("background", ct.c_void_p),
+                ("flags", ct.c_uint32)]
+
+
+class adop_frame(ct.Structure):
+    _fields_ = [("image", ct.c_void_p * ADOP_MAX_LEVELS), ("key", ct.c_void_p * ADOP_MAX_LEVELS),
+                ("count", ct.c_void_p * ADOP_MAX_LEVELS), ("acc", ct.c_void_p), ("out_dtype", ct.c_int32)]
+
+
+class adop_kernel_stat(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("total_ms", ct.c_double)]
+
+
+_P = ct.c_void_p
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol of include/adop.h
+SIGNATURES = {
+    "adop_workspace_bytes": (ct.c_size_t, [_P, _P, ct.c_int32, _P]),
+    "adop_render_forward": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, ct.c_size_t, _P]),
+    "adop_render_backward": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ct.c_size_t, _P]),
+    "adop_last_error": (ct.c_char_p, []),
+    "adop_abi_version": (ct.c_int32, []),
+    "adop_profile_enable": (ct.c_int, [ct.c_int32]),
+    "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load ``libadop.so`` (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run build())")
+        lib = ct.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise AdopError(st, load().adop_last_error().decode())
+
+
+def _dev_ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(dt) -> int:
+    torch = _torch()
+    if dt == torch.float32:
+        return ADOP_F32
+    if dt == torch.bfloat16:
+        return ADOP_BF16
+    if dt == torch.float16:
+        return ADOP_F16
+    raise ValueError(f"unsupported dtype {dt}")
+
+
+@dataclass
+class Points:
+    """The point cloud: xyz (n x 3 float32), feat (n x c float32/bfloat16/float16), optional normals."""
+    xyz: object
+    feat: object
+    normals: object = None
+
+    def struct(self) -> adop_points:
+        n, c = self.feat.shape
+        assert tuple(self.xyz.shape) == (n, 3)
+        return adop_points(n, c, dtype_code(self.feat.dtype), _dev_ptr(self.xyz), _dev_ptr(self.feat),
+                           _dev_ptr(self.normals))
+
+
+@dataclass
+class Params:
+    levels: int = 4
+    alpha: float = 0.01
+    znear: float = 1e-3
+    background: object = None  # c float32 CUDA tensor or None
+    flags: int = 0
+
+    def struct(self) -> adop_params:
+        return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags)
+
+
+def camera_struct(cam, crf_lut=None) -> adop_camera:
+    """Marshal a camera (attributes w, h, fx, fy, cx, cy, k1, k2, k3, p1, p2, R,
+    t; optionally ev, wb, vig_c, vig_a and epilogue) into adop_camera.
+    crf_lut: 3 x n float32 CUDA tensor of the response curve, or None."""
+    K = adop_intrinsics(int(cam.w), int(cam.h), *[float(getattr(cam, k, 0.0)) for k in
+                                                  ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    T = adop_pose((ct.c_float * 9)(*R.tolist()), (ct.c_float * 3)(*t.tolist()))
+    ph = adop_photometric(
+        float(getattr(cam, "ev", 0.0)), (ct.c_float * 3)(*[float(v) for v in getattr(cam, "wb", (1, 1, 1))]),
+        (ct.c_float * 2)(*[float(v) for v in getattr(cam, "vig_c", (0.5, 0.5))]),
+        (ct.c_float * 3)(*[float(v) for v in getattr(cam, "vig_a", (0, 0, 0))]),
+        _dev_ptr(crf_lut), 0 if crf_lut is None else int(crf_lut.shape[-1]),
+        1 if getattr(cam, "epilogue", False) else 0)
+    return adop_camera(K, T, ph)
+
+
+def pyramid_offsets(w: int, h: int, levels: int):
+    off = [0]
+    for l in range(levels):
+        off.append(off[-1] + (w >> l) * (h >> l))
+    return off
+
+
+@dataclass
+class Frame:
+    """One camera's outputs and per-pixel state (torch tensors)."""
+    images: list
+    key: object = None     # int64 (bit pattern of uint64), all layers concatenated
+    count: object = None   # int32 (bit pattern of uint32)
+    acc: object = None     # float32, pixel-major sums
+    w: int = 0
+    h: int = 0
+    levels: int = 0
+    keep: list = field(default_factory=list)
+
+    @staticmethod
+    def alloc(cam, c: int, levels: int, out_dtype=None, keep_state: bool = True, device="cuda"):
+        torch = _torch()
+        out_dtype = out_dtype or torch.float32
+        w, h = int(cam.w), int(cam.h)
+        images = [torch.empty((c, h >> l, w >> l), dtype=out_dtype, device=device) for l in range(levels)]
+        f = Frame(images, w=w, h=h, levels=levels)
+        if keep_state:
+            px = pyramid_offsets(w, h, levels)[-1]
+            f.key = torch.empty(px, dtype=torch.int64, device=device)
+            f.count = torch.empty(px, dtype=torch.int32, device=device)
+            f.acc = torch.empty(px * c, dtype=torch.float32, device=device)
+        return f
+
+    def layer(self, buf, l):
+        off = pyramid_offsets(self.w, self.h, self.levels)
+        return buf[off[l]:off[l + 1]].view(self.h >> l, self.w >> l)
+
+    def struct(self) -> adop_frame:
+        fr = adop_frame()
+        off = pyramid_offsets(self.w, self.h, self.levels)
+        for l, im in enumerate(self.images):
+            fr.image[l] = _dev_ptr(im)
+        if self.key is not None:
+            for l in range(self.levels):
+                fr.key[l] = self.key.data_ptr() + 8 * off[l]
+                fr.count[l] = self.count.data_ptr() + 4 * off[l]
+            fr.acc = self.acc.data_ptr()
+        fr.out_dtype = dtype_code(self.images[0].dtype) if self.images else ADOP_F32
+        return fr
+
+
+def _cams_array(cams, crf_luts=None):
+    arr = (adop_camera * len(cams))()
+    for k, cam in enumerate(cams):
+        arr[k] = camera_struct(cam, None if crf_luts is None else crf_luts[k])
+    return arr
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def adop_abi_version() -> int:
+    return int(load().adop_abi_version())
+
+
+def adop_profile_enable(on: bool = True) -> None:
+    _check(load().adop_profile_enable(1 if on else 0))
+
+
+def adop_profile_collect() -> dict:
+    """{kernel name: (launches, total device ms)} since the last collect."""
+    lib = load()
+    buf = (adop_kernel_stat * 64)()
+    m = lib.adop_profile_collect(buf, 64)
+    if m < 0:
+        raise AdopError(4, lib.adop_last_error().decode())
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(m)}
+
+
+def adop_last_error() -> str:
+    return load().adop_last_error().decode()
+
+
+def adop_workspace_bytes(points: Points, cams, params: Params, crf_luts=None) -> int:
+    lib = load()
+    ps, pr = points.struct(), params.struct()
+    arr = _cams_array(cams, crf_luts)
+    n = lib.adop_workspace_bytes(ct.byref(ps), arr, len(cams), ct.byref(pr))
+    if n == 0:
+        raise AdopError(1, lib.adop_last_error().decode())
+    return int(n)
+
+
+def alloc_workspace(points: Points, cams, params: Params, crf_luts=None, device="cuda"):
+    torch = _torch()
+    nbytes = adop_workspace_bytes(points, cams, params, crf_luts)
+    return torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+
+
+def _ws_ptr(ws):
+    """256-byte aligned pointer and usable size of a workspace tensor."""
+    p = ws.data_ptr()
+    a = (p + 255) // 256 * 256
+    return ct.c_void_p(a), ws.numel() - (a - p)
+
+
+def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):
+    """Forward pass (Sec. 3.1) of every camera; fills each frame's images and state."""
+    lib = load()
+    ps, pr = points.struct(), params.struct()
+    arr = _cams_array(cams, crf_luts)
+    fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
+    wp, wn = _ws_ptr(workspace)
+    _check(lib.adop_render_forward(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, wp, wn, _stream_ptr(stream)))
+
+
+def adop_render_backward(points: Points, cams, params: Params, frames, grad_images, grad_feat=None,
+                         grad_xyz=None, grad_pose=None, grad_intr=None, workspace=None, stream=None,
+                         crf_luts=None):
+    """Backward pass (Sec. 3.1).  grad_images[k][l]: dL/dI of camera k, layer l
+    (float32 CUDA tensor c x h_l x w_l or None)."""
+    lib = load()
+    ps, pr = points.struct(), params.struct()
+    arr = _cams_array(cams, crf_luts)
+    fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
+    L = params.levels
+    gptr = (ct.c_void_p * (len(cams) * L))()
+    for k in range(len(cams)):
+        for l in range(L):
+            g = grad_images[k][l] if grad_images is not None and grad_images[k] is not None else None
+            if g is not None and g.dtype != _torch().float32:
+                raise ValueError("grad_images must be float32")
+            gptr[k * L + l] = _dev_ptr(g)
+    wp, wn = _ws_ptr(workspace)
+    _check(lib.adop_render_backward(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr, _dev_ptr(grad_feat),
+                                    _dev_ptr(grad_xyz), _dev_ptr(grad_pose), _dev_ptr(grad_intr), wp, wn,
+                                    _stream_ptr(stream)))

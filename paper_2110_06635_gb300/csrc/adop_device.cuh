@@ -1,0 +1,219 @@
+// Device-side building blocks of the rasterizer: per-launch camera constants,
+// the FP32 projection (Sec. 3.1, P_l = 2^-l C(Rx + t)), rounding to pixels
+// (Eq. round, Eq. boundscheck), descriptor loads and vector atomics.
+//
+// The projection is written with explicit round-to-nearest intrinsics
+// (__fmul_rn / __fadd_rn / __fdiv_rn) so that no multiply-add is contracted:
+// every pixel and depth is the result of one fixed sequence of IEEE binary32
+// operations, which keeps depth/index buffers reproducible bit for bit.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/adop.h"
+
+namespace adop {
+
+constexpr int kMaxCamsPerLaunch = 16;
+constexpr int kThreads = 256;
+
+// Everything a kernel needs to know about one camera, passed by value in the
+// kernel's parameter space (uniform per block: blockIdx.y selects the camera).
+struct DevCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+  int32_t w, h;
+  int64_t off[ADOP_MAX_LEVELS + 1];  // first pixel of each layer in the concatenated pyramid
+  unsigned long long* key[ADOP_MAX_LEVELS];
+  uint32_t* cnt[ADOP_MAX_LEVELS];
+  void* image[ADOP_MAX_LEVELS];
+  const float* grad[ADOP_MAX_LEVELS];
+  float* acc;  // pixel-major FP32 sums, c floats per pixel
+  float* rec;  // backward records, kRecStride(c) floats per pixel
+  // photometric epilogue (Sec. 3.3); ev_scale = 2^-EV, computed on the host
+  int32_t epi;
+  int32_t crf_n;
+  float ev_scale;
+  float wb[3];
+  float vig_c[2];
+  float vig_a[3];
+  const float* crf;
+};
+
+struct LaunchCams {
+  DevCam c[kMaxCamsPerLaunch];
+};
+
+// Backward record of a pixel: [min_z, |Lambda|, <G, I>, G_0 .. G_{c-1}], padded
+// to a multiple of 4 floats so that each record starts on 16 bytes.
+__host__ __device__ constexpr int rec_stride(int c) { return ((c + 3) + 3) / 4 * 4; }
+
+// ---------------------------------------------------------------------------
+// FP32 projection contract
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void transform(const DevCam& cam, float x0, float x1, float x2,
+                                          float& X0, float& X1, float& X2) {
+  X0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cam.R[0], x0), __fmul_rn(cam.R[1], x1)),
+                           __fmul_rn(cam.R[2], x2)), cam.t[0]);
+  X1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cam.R[3], x0), __fmul_rn(cam.R[4], x1)),
+                           __fmul_rn(cam.R[5], x2)), cam.t[1]);
+  X2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cam.R[6], x0), __fmul_rn(cam.R[7], x1)),
+                           __fmul_rn(cam.R[8], x2)), cam.t[2]);
+}
+
+// Camera model C: layer-0 pixel coordinates of a camera-space point.
+__device__ __forceinline__ void camera(const DevCam& cam, float X0, float X1, float X2, float& u0,
+                                       float& v0) {
+  const float xn = __fdiv_rn(X0, X2);
+  const float yn = __fdiv_rn(X1, X2);
+  const float r2 = __fadd_rn(__fmul_rn(xn, xn), __fmul_rn(yn, yn));
+  const float d = __fadd_rn(
+      1.0f, __fmul_rn(r2, __fadd_rn(cam.k1, __fmul_rn(r2, __fadd_rn(cam.k2, __fmul_rn(r2, cam.k3))))));
+  const float a = __fmul_rn(xn, yn);
+  const float tx = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, cam.p1), a),
+                             __fmul_rn(cam.p2, __fadd_rn(r2, __fmul_rn(2.0f, __fmul_rn(xn, xn)))));
+  const float ty = __fadd_rn(__fmul_rn(cam.p1, __fadd_rn(r2, __fmul_rn(2.0f, __fmul_rn(yn, yn)))),
+                             __fmul_rn(__fmul_rn(2.0f, cam.p2), a));
+  const float xd = __fadd_rn(__fmul_rn(xn, d), tx);
+  const float yd = __fadd_rn(__fmul_rn(yn, d), ty);
+  u0 = __fadd_rn(__fmul_rn(cam.fx, xd), cam.cx);
+  v0 = __fadd_rn(__fmul_rn(cam.fy, yd), cam.cy);
+}
+
+// Eq. normalculling as printed: keep iff (R n)^T (R x + t) > 0.
+__device__ __forceinline__ bool normal_keep(const DevCam& cam, const float* nrm, int64_t i, float X0,
+                                            float X1, float X2) {
+  const float n0 = nrm[3 * i], n1 = nrm[3 * i + 1], n2 = nrm[3 * i + 2];
+  const float r0 = __fadd_rn(__fadd_rn(__fmul_rn(cam.R[0], n0), __fmul_rn(cam.R[1], n1)), __fmul_rn(cam.R[2], n2));
+  const float r1 = __fadd_rn(__fadd_rn(__fmul_rn(cam.R[3], n0), __fmul_rn(cam.R[4], n1)), __fmul_rn(cam.R[5], n2));
+  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(cam.R[6], n0), __fmul_rn(cam.R[7], n1)), __fmul_rn(cam.R[8], n2));
+  const float dot = __fadd_rn(__fadd_rn(__fmul_rn(r0, X0), __fmul_rn(r1, X1)), __fmul_rn(r2, X2));
+  return dot > 0.0f;
+}
+
+// Exact 2^-l.
+__device__ __forceinline__ float layer_scale(int l) { return __int_as_float((127 - l) << 23); }
+
+// Eq. round (nearest, ties to even) + Eq. boundscheck at layer l.  Coordinates
+// outside ]-1, w_l + 1[ (and NaN) are rejected before the integer conversion.
+__device__ __forceinline__ bool pixel_at(float u0, float v0, int l, int32_t w, int32_t h, int32_t& pu,
+                                         int32_t& pv) {
+  const int32_t wl = w >> l, hl = h >> l;
+  const float s = layer_scale(l);
+  const float ul = __fmul_rn(u0, s), vl = __fmul_rn(v0, s);
+  if (!(ul > -1.0f && ul < __fadd_rn((float)wl, 1.0f))) return false;
+  if (!(vl > -1.0f && vl < __fadd_rn((float)hl, 1.0f))) return false;
+  pu = __float2int_rn(ul);
+  pv = __float2int_rn(vl);
+  return pu >= 0 && pu < wl && pv >= 0 && pv < hl;
+}
+
+__device__ __forceinline__ unsigned long long depth_key(float z, int64_t i) {
+  return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)(uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// storage types
+// ---------------------------------------------------------------------------
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// Load the C descriptors of point i (row-major n x C) as FP32, with the widest
+// aligned vector loads the row size allows (rows start 16-byte aligned when
+// C * sizeof(T) is a multiple of 16).
+template <int C, typename T>
+__device__ __forceinline__ void load_feat(const T* __restrict__ feat, int64_t i, float (&f)[C]) {
+  constexpr int kBytes = C * (int)sizeof(T);
+  const T* row = feat + i * C;
+  if constexpr (kBytes % 16 == 0) {
+    constexpr int kVec = kBytes / 16;
+    constexpr int kPer = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) {
+      uint4 raw = __ldg(reinterpret_cast<const uint4*>(row) + v);
+      const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) f[v * kPer + k] = to_f32<T>(e[k]);
+    }
+  } else if constexpr (kBytes % 8 == 0) {
+    constexpr int kVec = kBytes / 8;
+    constexpr int kPer = 8 / (int)sizeof(T);
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) {
+      uint2 raw = __ldg(reinterpret_cast<const uint2*>(row) + v);
+      const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) f[v * kPer + k] = to_f32<T>(e[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < C; ++k) f[k] = to_f32<T>(row[k]);
+  }
+}
+
+// acc[0..C) += f (FP32), as few global atomics as the alignment allows
+// (sm_90+ has float2/float4 vector atomics on global memory).
+template <int C>
+__device__ __forceinline__ void atomic_add_vec(float* a, const float (&f)[C]) {
+  if constexpr (C % 4 == 0) {
+#pragma unroll
+    for (int v = 0; v < C / 4; ++v)
+      atomicAdd(reinterpret_cast<float4*>(a) + v, make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]));
+  } else if constexpr (C % 2 == 0) {
+#pragma unroll
+    for (int v = 0; v < C / 2; ++v) atomicAdd(reinterpret_cast<float2*>(a) + v, make_float2(f[2 * v], f[2 * v + 1]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < C; ++k) atomicAdd(a + k, f[k]);
+  }
+}
+
+// Layer of a pixel index g in [0, off[levels]).
+__device__ __forceinline__ int layer_of(const DevCam& cam, int levels, int64_t g) {
+  int l = 0;
+#pragma unroll
+  for (int k = 1; k < ADOP_MAX_LEVELS; ++k)
+    if (k < levels && g >= cam.off[k]) l = k;
+  return l;
+}
+
+// Photometric model of Sec. 3.3 on one value of channel ch at layer-0 pixel
+// (u, v); if dydx is given it receives d out / d in.
+__device__ __forceinline__ float epilogue(const DevCam& cam, int ch, int32_t u, int32_t v, float x,
+                                          float* dydx) {
+  const float ru = __fdiv_rn((float)u, (float)cam.w) - cam.vig_c[0];
+  const float rv = __fdiv_rn((float)v, (float)cam.h) - cam.vig_c[1];
+  const float r2 = ru * ru + rv * rv;
+  const float vig = 1.0f + r2 * (cam.vig_a[0] + r2 * (cam.vig_a[1] + r2 * cam.vig_a[2]));
+  const float scale = cam.ev_scale * cam.wb[ch] * vig;
+  const float xs = x * scale;
+  float y = xs, dy = 1.0f;
+  if (cam.crf != nullptr && cam.crf_n >= 2) {
+    const int n = cam.crf_n;
+    const float xc = fminf(fmaxf(xs, 0.0f), 1.0f);
+    const float pos = xc * (float)(n - 1);
+    int i0 = (int)floorf(pos);
+    i0 = min(i0, n - 2);
+    const float fr = pos - (float)i0;
+    const float* lut = cam.crf + ch * n;
+    const float a = __ldg(lut + i0), b = __ldg(lut + i0 + 1);
+    y = a * (1.0f - fr) + b * fr;
+    dy = (xs < 0.0f || xs > 1.0f) ? 0.0f : (b - a) * (float)(n - 1);
+  }
+  if (dydx) *dydx = dy * scale;
+  return y;
+}
+
+}  // namespace adop

@@ -1,0 +1,192 @@
+// Forward pass of the one-pixel point rasterizer (Sec. 3.1): a depth-only
+// pass, an accumulate pass for the points that pass the fuzzy depth test and
+// a per-pixel normalise pass (the three-pass structure of the paper's
+// implementation details), preceded by a clear of the per-pixel state.
+//
+// Work decomposition: blockIdx.y selects the camera; blocks stride over
+// points (or pixels) with a grid sized to a few waves of the GPU's SMs.
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace adop {
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int point_blocks(int64_t n, int ncam) {
+  const int64_t want = (n + kThreads - 1) / kThreads;
+  const int64_t cap = ((int64_t)num_sms() * 8 + ncam - 1) / ncam;
+  int64_t b = want < cap ? want : cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------------------
+// clear: key = UINT64_MAX (empty), count = 0, acc = 0 for every pixel
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ LaunchCams cams,
+                                                    const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int64_t total = cam.off[a.levels];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int l = layer_of(cam, a.levels, g);
+    const int64_t p = g - cam.off[l];
+    cam.key[l][p] = ~0ull;
+    cam.cnt[l][p] = 0u;
+    float* acc = cam.acc + g * C;
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+      for (int v = 0; v < C / 4; ++v) reinterpret_cast<float4*>(acc)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int k = 0; k < C; ++k) acc[k] = 0.0f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1 depth pass: key[l][p] = min over points of (bits(z) << 32 | i)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
+                                                    const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float X0, X1, X2, u0, v0;
+    transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
+    if (!(X2 > a.znear)) continue;
+    if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
+    camera(cam, X0, X1, X2, u0, v0);
+    const unsigned long long key = depth_key(X2, i);
+    for (int l = 0; l < a.levels; ++l) {
+      int32_t pu, pv;
+      if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
+      unsigned long long* slot = cam.key[l] + (int64_t)pv * (cam.w >> l) + pu;
+      // most points are occluded: read first, issue the atomic only if it can win
+      if (key < __ldcg(slot)) atomicMin(slot, key);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2 accumulate: points with z <= f32(z_min * (1 + alpha)) add their
+// descriptor to the pixel's FP32 sum and increment |Lambda|
+// ---------------------------------------------------------------------------
+template <int C, typename TF>
+__global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ LaunchCams cams,
+                                                    const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const TF* feat = reinterpret_cast<const TF*>(a.feat);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float X0, X1, X2, u0, v0;
+    transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
+    if (!(X2 > a.znear)) continue;
+    if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
+    camera(cam, X0, X1, X2, u0, v0);
+    float f[C];
+    bool loaded = false;
+    for (int l = 0; l < a.levels; ++l) {
+      int32_t pu, pv;
+      if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
+      const int64_t p = (int64_t)pv * (cam.w >> l) + pu;
+      const float minz = __uint_as_float((uint32_t)(__ldg(cam.key[l] + p) >> 32));
+      if (!(X2 <= __fmul_rn(minz, a.a1))) continue;
+      if (!loaded) {
+        load_feat<C, TF>(feat, i, f);
+        loaded = true;
+      }
+      atomic_add_vec<C>(cam.acc + (cam.off[l] + p) * C, f);
+      atomicAdd(cam.cnt[l] + p, 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3 normalise: I = sum / |Lambda| (Eq. blend), background where empty,
+// photometric epilogue on layer 0, cast to the output type, planar layout
+// ---------------------------------------------------------------------------
+template <int C, typename TO>
+__global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ LaunchCams cams,
+                                                        const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int64_t total = cam.off[a.levels];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int l = layer_of(cam, a.levels, g);
+    TO* img = reinterpret_cast<TO*>(cam.image[l]);
+    if (img == nullptr) continue;
+    const int64_t p = g - cam.off[l];
+    const int64_t np = cam.off[l + 1] - cam.off[l];
+    const uint32_t n = cam.cnt[l][p];
+    float v[C];
+    if (n == 0) {
+#pragma unroll
+      for (int k = 0; k < C; ++k) v[k] = a.background ? __ldg(a.background + k) : 0.0f;
+    } else {
+      const float* acc = cam.acc + g * C;
+      const float fn = (float)n;
+      if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+          const float4 s = reinterpret_cast<const float4*>(acc)[q];
+          v[4 * q] = __fdiv_rn(s.x, fn);
+          v[4 * q + 1] = __fdiv_rn(s.y, fn);
+          v[4 * q + 2] = __fdiv_rn(s.z, fn);
+          v[4 * q + 3] = __fdiv_rn(s.w, fn);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) v[k] = __fdiv_rn(acc[k], fn);
+      }
+    }
+    if (l == 0 && cam.epi) {
+      const int32_t pu = (int32_t)(p % cam.w), pv = (int32_t)(p / cam.w);
+#pragma unroll
+      for (int k = 0; k < (C < 3 ? C : 3); ++k) v[k] = epilogue(cam, k, pu, pv, v[k], nullptr);
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) img[k * np + p] = from_f32<TO>(v[k]);
+  }
+}
+
+dim3 pixel_grid(const LaunchCams& cams, const PointArgs& a) {
+  int64_t most = 0;
+  for (int k = 0; k < a.ncam; ++k) most = cams.c[k].off[a.levels] > most ? cams.c[k].off[a.levels] : most;
+  int64_t want = (most + kThreads - 1) / kThreads;
+  int64_t cap = ((int64_t)num_sms() * 8 + a.ncam - 1) / a.ncam;
+  int64_t b = want < cap ? want : cap;
+  return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)a.ncam);
+}
+
+cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
+  ADOP_DISPATCH_C(c, k_clear<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  k_depth<<<dim3(point_blocks(a.n, a.ncam), a.ncam), kThreads, 0, s>>>(cams, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF><<<grid, kThreads, 0, s>>>(cams, a)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, k_normalize<kC, TO><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a)));
+  return cudaGetLastError();
+}
+
+}  // namespace adop

@@ -1,0 +1,73 @@
+// Host-side launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adop_device.cuh"
+
+namespace adop {
+
+// Arguments shared by the point kernels of one launch.
+struct PointArgs {
+  const float* xyz;
+  const void* feat;
+  const float* normals;  // non-NULL only when normal culling is on
+  const float* background;
+  int64_t n;
+  int32_t levels;
+  int32_t ncam;         // cameras in this launch (<= kMaxCamsPerLaunch)
+  float znear;
+  float a1;             // f32(1 + alpha)
+  uint32_t flags;
+};
+
+// Backward outputs of one launch.
+enum GradMode : int32_t { kGradAssign = 0, kGradAccumulate = 1, kGradAtomic = 2 };
+
+struct BwdArgs {
+  float* grad_feat;
+  float* grad_xyz;
+  float* partials;      // [ncam][blocks_x][12] pose (6) + intrinsics (6) block sums
+  int32_t mode;         // GradMode
+  int32_t all_projected;
+};
+
+int num_sms();
+int point_blocks(int64_t n, int ncam);
+dim3 pixel_grid(const LaunchCams& cams, const PointArgs& a);
+
+cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s);
+cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s);
+cudaError_t launch_normalize(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s);
+cudaError_t launch_bwd_prepass(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s);
+cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c,
+                              adop_dtype fd, int blocks_x, cudaStream_t s);
+cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
+                              float* grad_intr, cudaStream_t s);
+
+// Channel counts with compiled kernels.
+inline bool channels_supported(int c) { return c == 1 || c == 2 || c == 3 || c == 4 || c == 8 || c == 16; }
+
+}  // namespace adop
+
+// Dispatch a runtime channel count to a compile-time constant kC.
+#define ADOP_DISPATCH_C(c, ...)                     \
+  switch (c) {                                      \
+    case 1: { constexpr int kC = 1; __VA_ARGS__; break; }  \
+    case 2: { constexpr int kC = 2; __VA_ARGS__; break; }  \
+    case 3: { constexpr int kC = 3; __VA_ARGS__; break; }  \
+    case 4: { constexpr int kC = 4; __VA_ARGS__; break; }  \
+    case 8: { constexpr int kC = 8; __VA_ARGS__; break; }  \
+    case 16: { constexpr int kC = 16; __VA_ARGS__; break; } \
+    default: return cudaErrorInvalidValue;          \
+  }
+
+#define ADOP_DISPATCH_T(dt, T, ...)                                   \
+  switch (dt) {                                                       \
+    case ADOP_F32: { using T = float; __VA_ARGS__; break; }           \
+    case ADOP_BF16: { using T = __nv_bfloat16; __VA_ARGS__; break; }  \
+    case ADOP_F16: { using T = __half; __VA_ARGS__; break; }          \
+    default: return cudaErrorInvalidValue;                            \
+  }

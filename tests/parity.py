@@ -1,0 +1,159 @@
+"""Helpers of the GPU-vs-oracle parity tests: run the CUDA library and the CPU
+oracle on the same seeded inputs and compare with the stated tolerances.
+
+Tolerances (relative, written from the arithmetic of each output):
+  keys, counts         bit-exact (integer results of the FP32 projection contract)
+  features (FP32 sums) |gpu - ref| <= 1e-5 * max(|ref|, rms(ref)) per element
+  BF16 / FP16 image    the same with 2e-2 (one BF16 rounding of the output is 2^-9)
+  per-point gradients  |gpu - ref| <= 1e-4 * max(|ref|, rms(ref)) per element
+  pose / intrinsics    |gpu - ref| <= 1e-4 * sum over (point, layer) of |term|
+"""
+from __future__ import annotations
+
+import numpy as np
+
+RTOL_FEAT_F32 = 1e-5
+RTOL_FEAT_LOWP = 2e-2
+RTOL_GRAD = 1e-4
+RTOL_REDUCED = 1e-4
+
+U64_MAX = np.iinfo(np.uint64).max
+
+
+def rel_err(gpu, ref):
+    """max over elements of |gpu - ref| / max(|ref|, rms(ref))."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return 0.0
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    den = np.maximum(np.abs(ref), rms)
+    den = np.where(den == 0, 1.0, den)
+    return float(np.max(np.abs(gpu - ref) / den))
+
+
+def assert_close(gpu, ref, rtol, what=""):
+    e = rel_err(gpu, ref)
+    assert e <= rtol, f"{what}: relative error {e:.3e} > {rtol:.1e}"
+    return e
+
+
+def assert_reduced(gpu, ref, abs_sum, rtol=RTOL_REDUCED, what=""):
+    gpu, ref, abs_sum = (np.asarray(v, np.float64) for v in (gpu, ref, abs_sum))
+    bound = rtol * np.maximum(abs_sum, 1e-30)
+    bad = np.abs(gpu - ref) > bound
+    assert not bad.any(), f"{what}: gpu {gpu} ref {ref} bound {bound}"
+
+
+def torch_dtype(name):
+    import torch
+    return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[name]
+
+
+def feat_tensor(scene, dtype: str, device="cuda"):
+    import torch
+    f = scene.feat_as(dtype)
+    if dtype == "bf16":
+        return torch.from_numpy(f.view(np.int16).copy()).to(device).view(torch.bfloat16)
+    return torch.from_numpy(np.ascontiguousarray(f)).to(device)
+
+
+def to_np(t):
+    import torch
+    if t.dtype == torch.bfloat16:
+        return t.float().cpu().numpy()
+    return t.cpu().numpy()
+
+
+def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, flags=0,
+            grads=None, out_dtype="f32", keep_state=True, backward=True, normals=False, crf=True,
+            grad_assign=False, init=0.0):
+    """Forward (+ backward) through the C ABI; returns numpy results."""
+    import torch
+    dev = "cuda"
+    xyz = torch.from_numpy(scene.xyz).to(dev)
+    feat = feat_tensor(scene, dtype, dev)
+    nrm = torch.from_numpy(scene.normals).to(dev) if normals else None
+    pts = adop.Points(xyz, feat, nrm)
+    bg = None if background is None else torch.tensor(np.asarray(background, np.float32), device=dev)
+    if grad_assign:
+        flags |= adop.ADOP_FLAG_GRAD_ASSIGN
+    params = adop.Params(levels, alpha, znear, bg, flags)
+    luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(dev)
+            if (crf and getattr(c, "crf", None) is not None) else None for c in cams]
+    frames = [adop.Frame.alloc(c, scene.c, levels, torch_dtype(out_dtype), keep_state, dev) for c in cams]
+    ws = adop.alloc_workspace(pts, cams, params, luts, dev)
+    adop.adop_render_forward(pts, cams, params, frames, ws, crf_luts=luts)
+    out = {"frames": frames}
+    if keep_state:
+        out["keys"] = [f.key.cpu().numpy().view(np.uint64) for f in frames]
+        out["cnt"] = [f.count.cpu().numpy().view(np.uint32) for f in frames]
+    out["img"] = [np.concatenate([to_np(im).ravel() for im in f.images]) for f in frames]
+    if backward:
+        n, c = scene.n, scene.c
+        gfeat = torch.full((n, c), init, dtype=torch.float32, device=dev)
+        gxyz = torch.full((n, 3), init, dtype=torch.float32, device=dev)
+        gpose = torch.full((len(cams), 6), init, dtype=torch.float32, device=dev)
+        gintr = torch.full((len(cams), 6), init, dtype=torch.float32, device=dev)
+        gimgs = [[torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in gk] for gk in grads]
+        adop.adop_render_backward(pts, cams, params, frames, gimgs, gfeat, gxyz, gpose, gintr, ws, crf_luts=luts)
+        torch.cuda.synchronize()
+        out["dfeat"] = gfeat.cpu().numpy().astype(np.float64) - init
+        out["dxyz"] = gxyz.cpu().numpy().astype(np.float64) - init
+        out["dpose"] = gpose.cpu().numpy().astype(np.float64) - init
+        out["dintr"] = gintr.cpu().numpy().astype(np.float64) - init
+    torch.cuda.synchronize()
+    return out
+
+
+def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
+               normals=False, epilogue=False, all_projected=False, backward=True):
+    """The oracle on the same inputs: per camera forward (+ backward), summed
+    over cameras for the per-point gradients."""
+    feat = scene.feat_as(dtype)
+    res = {"keys": [], "cnt": [], "img": [], "dpose": [], "dintr": [], "dpose_abs": [], "dintr_abs": []}
+    dfeat = np.zeros((scene.n, scene.c))
+    dxyz = np.zeros((scene.n, 3))
+    for k, cam in enumerate(cams):
+        f = orc.forward(scene.xyz, feat, cam, levels, alpha, znear, background,
+                        scene.normals if normals else None)
+        res["keys"].append(f.keys)
+        res["cnt"].append(f.cnt)
+        img = f.img.copy()
+        G = None if grads is None else np.concatenate([np.asarray(g, np.float64).ravel() for g in grads[k]])
+        if epilogue and getattr(cam, "epilogue", False):
+            c, h, w = scene.c, cam.h, cam.w
+            img0, dgain = orc.epilogue(f.img[:c * h * w].reshape(c, h, w), cam.ev, cam.wb, cam.vig_c, cam.vig_a,
+                                       cam.crf, want_grad=True)
+            img[:c * h * w] = img0.ravel()
+            if G is not None:
+                G = G.copy()
+                G[:c * h * w] *= dgain.ravel()
+        res["img"].append(img)
+        if backward and G is not None:
+            b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected)
+            dfeat += b.dfeat
+            dxyz += b.dxyz
+            for key in ("dpose", "dintr", "dpose_abs", "dintr_abs"):
+                res[key].append(getattr(b, key))
+    res["dfeat"], res["dxyz"] = dfeat, dxyz
+    return res
+
+
+def compare(gpu, ref, dtype="f32", out_dtype="f32", check_state=True, backward=True):
+    """Assert parity of every output; returns the measured relative errors."""
+    errs = {}
+    rt_img = RTOL_FEAT_F32 if out_dtype == "f32" else RTOL_FEAT_LOWP
+    for k in range(len(ref["img"])):
+        if check_state:
+            assert np.array_equal(gpu["keys"][k], ref["keys"][k]), \
+                f"camera {k}: {(gpu['keys'][k] != ref['keys'][k]).sum()} keys differ"
+            assert np.array_equal(gpu["cnt"][k], ref["cnt"][k]), f"camera {k}: counts differ"
+        errs[f"img{k}"] = assert_close(gpu["img"][k], ref["img"][k], rt_img, f"camera {k} image")
+    if backward:
+        errs["dfeat"] = assert_close(gpu["dfeat"], ref["dfeat"], RTOL_GRAD, "dL/dtau")
+        errs["dxyz"] = assert_close(gpu["dxyz"], ref["dxyz"], RTOL_GRAD, "dL/dx")
+        for k in range(len(ref["dpose"])):
+            assert_reduced(gpu["dpose"][k], ref["dpose"][k], ref["dpose_abs"][k], what=f"camera {k} dL/dxi")
+            assert_reduced(gpu["dintr"][k], ref["dintr"][k], ref["dintr_abs"][k], what=f"camera {k} dL/dK")
+    return errs

@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every symbol that include/adop.h declares, and argument errors
+are reported synchronously, before any CUDA call."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2110_06635_gb300 as adop
+    adop.build()
+    return adop, adop.load()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(adop_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    adop, so = lib
+    names = declared_functions()
+    assert "adop_render_forward" in names and "adop_render_backward" in names
+    for name in names:
+        assert hasattr(so, name), f"{name} declared in include/ but not exported"
+    assert set(names) <= set(adop.SIGNATURES), "binding misses a declared entry point"
+    assert adop.adop_abi_version() == 1
+
+
+def _structs(adop, n=10, c=4, levels=4, w=64, h=48, flags=0):
+    from paper_2110_06635_gb300 import _abi as A
+    pts = A.adop_points(n, c, A.ADOP_F32, 0x10000, 0x20000, None)
+    K = A.adop_intrinsics(w, h, 50.0, 50.0, w / 2, h / 2, 0, 0, 0, 0, 0)
+    R = (ct.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    T = A.adop_pose(R, (ct.c_float * 3)(0, 0, 2))
+    cam = (A.adop_camera * 1)(A.adop_camera(K, T, A.adop_photometric()))
+    prm = A.adop_params(levels, 0.01, 1e-3, None, flags)
+    fr = (A.adop_frame * 1)()
+    return pts, cam, prm, fr
+
+
+def _fwd(so, pts, cam, prm, fr, ws=0x100000, nbytes=1 << 40, ncam=1):
+    return so.adop_render_forward(ct.byref(pts), cam, ncam, ct.byref(prm), fr, ws, nbytes, None)
+
+
+def test_workspace_bytes(lib):
+    adop, so = lib
+    pts, cam, prm, fr = _structs(adop)
+    n = so.adop_workspace_bytes(ct.byref(pts), cam, 1, ct.byref(prm))
+    px = 64 * 48 + 32 * 24 + 16 * 12 + 8 * 6
+    assert n >= px * (8 + 4 + 16 + 32) and n % 256 == 0
+    prm.levels = 0
+    assert so.adop_workspace_bytes(ct.byref(pts), cam, 1, ct.byref(prm)) == 0
+    assert "levels" in so.adop_last_error().decode()
+
+
+@pytest.mark.parametrize("case,status,msg", [
+    ("ncam0", 1, "n_cam"), ("levels9", 1, "levels"), ("c5", 2, "channel count 5"), ("alpha", 1, "alpha"),
+    ("znear", 1, "znear"), ("flags", 1, "flag"), ("cull", 1, "normals"), ("size", 1, "image size"),
+    ("small", 1, "too small"), ("ws", 3, "workspace"), ("wsalign", 1, "aligned"), ("feat", 1, "16-byte"),
+    ("mixed", 1, "all set or all NULL"), ("nan", 1, "non-finite"), ("dtype", 1, "dtype"),
+])
+def test_invalid_arguments_fail_synchronously(lib, case, status, msg):
+    adop, so = lib
+    pts, cam, prm, fr = _structs(adop)
+    kw = {}
+    if case == "ncam0":
+        kw["ncam"] = 0
+    elif case == "levels9":
+        prm.levels = 9
+    elif case == "c5":
+        pts.c = 5
+    elif case == "alpha":
+        prm.alpha = -1.0
+    elif case == "znear":
+        prm.znear = float("nan")
+    elif case == "flags":
+        prm.flags = 1 << 12
+    elif case == "cull":
+        prm.flags = adop.ADOP_FLAG_NORMAL_CULL
+    elif case == "size":
+        cam[0].K.w = 0
+    elif case == "small":
+        cam[0].K.w = 4
+    elif case == "ws":
+        kw["nbytes"] = 1024
+    elif case == "wsalign":
+        kw["ws"] = 0x100010
+    elif case == "feat":
+        pts.feat = 0x20008
+    elif case == "mixed":
+        fr[0].key[0] = 0x40000
+    elif case == "nan":
+        cam[0].T.t[1] = float("inf")
+    elif case == "dtype":
+        fr[0].out_dtype = 7
+    st = _fwd(so, pts, cam, prm, fr, **kw)
+    assert st == status
+    assert msg in so.adop_last_error().decode()
+
+
+def test_backward_validates_too(lib):
+    adop, so = lib
+    pts, cam, prm, fr = _structs(adop)
+    prm.levels = 12
+    st = so.adop_render_backward(ct.byref(pts), cam, 1, ct.byref(prm), fr, None, None, None, None, None,
+                                 0x100000, 1 << 40, None)
+    assert st == 1 and "levels" in so.adop_last_error().decode()

@@ -1,0 +1,159 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.  Keys and counts bit-exact; features and gradients
+within the tolerances stated in tests/parity.py."""
+import numpy as np
+import pytest
+
+import scenes
+from parity import compare, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _grads(cams, c, levels, seed):
+    return [scenes.upstream_grad(cam.w, cam.h, levels, c, seed + k) for k, cam in enumerate(cams)]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return scenes.config(1)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_tiny_config_fwd_bwd(adop, orc, tiny, dtype):
+    """20,000 points on 3 spheres, 256^2, C = 4, L = 4, alpha = 0.01."""
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 7)
+    g = gpu_run(adop, sc, cams, dtype, grads=G)
+    r = oracle_run(orc, sc, cams, dtype, grads=G)
+    compare(g, r, dtype)
+
+
+@pytest.mark.parametrize("c", [1, 2, 3, 4, 8, 16])
+def test_channel_counts_ragged_image(adop, orc, c):
+    """Every compiled channel count on an odd-sized image (ragged layers and
+    tails) with a point count that is not a multiple of the block size."""
+    sc = scenes.tiny_spheres(4099, c, seed=31)
+    cam = scenes.Camera(193, 97, 160.0, 160.0, 96.3, 48.7, k1=0.02, k2=-0.01, p1=0.001, p2=-0.002,
+                        R=np.eye(3, dtype=np.float32), t=np.array([-0.4, -0.4, 2.2], np.float32))
+    G = _grads([cam], c, 4, 11)
+    bg = np.linspace(-0.5, 0.5, c)
+    g = gpu_run(adop, sc, [cam], "f32", background=bg, grads=G)
+    r = oracle_run(orc, sc, [cam], "f32", background=bg, grads=G)
+    compare(g, r)
+
+
+@pytest.mark.parametrize("out_dtype", ["bf16", "f16"])
+def test_low_precision_output(adop, orc, tiny, out_dtype):
+    sc, cams = tiny
+    g = gpu_run(adop, sc, cams, "bf16", out_dtype=out_dtype, backward=False)
+    r = oracle_run(orc, sc, cams, "bf16", backward=False)
+    compare(g, r, "bf16", out_dtype, backward=False)
+
+
+def test_recompute_matches_kept_state(adop, orc, tiny):
+    """Frames without key/count/acc: the backward re-renders (Sec. 3.1,
+    implementation details) and must give the kept-state results."""
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 7)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, keep_state=False)
+    r = oracle_run(orc, sc, cams, "f32", grads=G)
+    compare(g, r, check_state=False)
+
+
+def test_accumulate_and_assign(adop, orc, tiny):
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 7)
+    r = oracle_run(orc, sc, cams, "f32", grads=G)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, init=1.0)
+    compare(g, r)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, grad_assign=True)
+    compare(g, r)
+
+
+def test_multi_camera(adop, orc):
+    """Three views of one cloud in one call: per-point gradients sum over views."""
+    sc = scenes.tiny_spheres(6000, 4, seed=41)
+    cams = []
+    for k, (w, h) in enumerate([(160, 120), (131, 77), (96, 96)]):
+        R, t = scenes.look_at(np.array([np.cos(k), 0.3, np.sin(k)]) * 2.5 + 0.5, np.full(3, 0.5))
+        cams.append(scenes.Camera(w, h, 0.9 * w, 0.9 * w, w / 2, h / 2, k1=0.01, R=R, t=t))
+    G = _grads(cams, sc.c, 4, 17)
+    for assign in (False, True):
+        g = gpu_run(adop, sc, cams, "f32", grads=G, grad_assign=assign)
+        r = oracle_run(orc, sc, cams, "f32", grads=G)
+        compare(g, r)
+
+
+def test_all_projected_flag(adop, orc, tiny):
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 9)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, flags=adop.ADOP_FLAG_GRAD_ALL_PROJECTED)
+    r = oracle_run(orc, sc, cams, "f32", grads=G, all_projected=True)
+    compare(g, r)
+
+
+def test_normal_culling(adop, orc, tiny):
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 5)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, normals=True, flags=adop.ADOP_FLAG_NORMAL_CULL)
+    r = oracle_run(orc, sc, cams, "f32", grads=G, normals=True)
+    compare(g, r)
+
+
+def test_photometric_epilogue(adop, orc):
+    """Exposure, white balance, vignette and response curve on layer 0 (Sec. 3.3),
+    forward and chained into the backward."""
+    sc = scenes.tiny_spheres(8000, 4, seed=51)
+    cams = scenes.orbit_cameras(2, seed=52, radius=2.5, resolutions=((128, 96), (100, 75)))
+    for cam in cams:
+        R, t = scenes.look_at(-cam.R.T @ cam.t, np.full(3, 0.5))
+        cam.R, cam.t = R, t
+    sc.feat = np.abs(sc.feat) * 0.5  # radiance-like descriptors
+    G = _grads(cams, sc.c, 4, 53)
+    g = gpu_run(adop, sc, cams, "f32", grads=G, flags=adop.ADOP_FLAG_EPILOGUE)
+    r = oracle_run(orc, sc, cams, "f32", grads=G, epilogue=True)
+    compare(g, r)
+
+
+def test_empty_and_degenerate_inputs(adop, orc):
+    cam = scenes.tiny_camera()
+    bg = np.array([0.1, 0.2, 0.3, 0.4])
+    # no points at all: background everywhere, gradients untouched
+    empty = scenes.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32), np.zeros((0, 3), np.float32))
+    G = _grads([cam], 4, 4, 3)
+    g = gpu_run(adop, empty, [cam], "f32", background=bg, grads=G)
+    r = oracle_run(orc, empty, [cam], "f32", background=bg, grads=G)
+    compare(g, r)
+    # every point behind the camera (z <= znear) or outside the image
+    sc = scenes.tiny_spheres(3000, 4, seed=61)
+    behind = scenes.Camera(256, 256, 205.0, 205.0, 128.0, 128.0, R=np.eye(3, dtype=np.float32),
+                           t=np.array([0, 0, -5], np.float32))
+    g = gpu_run(adop, sc, [behind], "f32", background=bg, grads=G)
+    r = oracle_run(orc, sc, [behind], "f32", background=bg, grads=G)
+    compare(g, r)
+    assert np.all(g["cnt"][0] == 0)
+
+
+def test_exact_half_pixel_ties(adop, orc):
+    """Projections exactly on .5 pixel boundaries round half to even on both sides."""
+    w, h = 16, 8
+    cam = scenes.Camera(w, h, 1.0, 1.0, 0.0, 0.0, R=np.eye(3, dtype=np.float32), t=np.zeros(3, np.float32))
+    u = np.array([0.5, 1.5, 2.5, 3.5, 4.5, 7.5, 8.0, 15.5, 14.5, 6.5], np.float32)
+    v = np.array([0.5, 1.5, 2.5, 3.5, 4.5, 6.5, 7.5, 0.0, 2.0, 5.5], np.float32)
+    z = np.full(10, 2.0, np.float32)
+    xyz = np.stack([u * z, v * z, z], 1).astype(np.float32)
+    sc = scenes.Scene(xyz, np.arange(20, dtype=np.float32).reshape(10, 2), np.zeros((10, 3), np.float32))
+    G = _grads([cam], 2, 3, 4)
+    g = gpu_run(adop, sc, [cam], "f32", levels=3, grads=G)
+    r = oracle_run(orc, sc, [cam], "f32", levels=3, grads=G)
+    compare(g, r)
+
+
+def test_alpha_zero_and_large_alpha(adop, orc, tiny):
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 8)
+    for alpha in (0.0, 0.2):
+        g = gpu_run(adop, sc, cams, "f32", alpha=alpha, grads=G)
+        r = oracle_run(orc, sc, cams, "f32", alpha=alpha, grads=G)
+        compare(g, r)
