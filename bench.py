@@ -126,16 +126,18 @@ class ClockSampler:
         self.gpu_id = gpu_id
         self.proc = None
         self.lines = []
+        self.error = ""
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                         stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-        except (OSError, ValueError):
+        except (OSError, ValueError) as e:
             self.proc = None
+            self.error = repr(e)
         return self
 
     def _read(self):
@@ -167,9 +169,17 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            why = self.error or (self.lines[0][:160] if self.lines else "no output")
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "error": why}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def gpu_index(device) -> str:
+    """nvidia-smi id of a torch device: its UUID (robust to CUDA_VISIBLE_DEVICES)."""
+    import torch
+    u = str(torch.cuda.get_device_properties(device).uuid)
+    return u if u.startswith("GPU-") else f"GPU-{u}"
 
 
 def measured_peaks():
@@ -290,8 +300,7 @@ def run_ours(args, dist, rank, world):
         torch.cuda.synchronize()
         adop.adop_profile_enable(True)
         adop.adop_profile_collect()
-        gpu_uuid = str(torch.cuda.get_device_properties(device).uuid)
-        sampler = ClockSampler(gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}")
+        sampler = ClockSampler(gpu_index(device))
         with sampler:
             total_ms, per = timed_steps(lambda: wl.step(sp), args.steps, flush, dist, device)
         kstats = adop.adop_profile_collect()
