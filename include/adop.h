@@ -180,6 +180,41 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
                                  float* grad_pose, float* grad_intr, void* workspace,
                                  size_t workspace_bytes, adop_stream stream);
 
+/*
+ * Backward pass that allocates nothing and takes no workspace.
+ * The paper has no counterpart: this is a deployment variant of
+ * adop_render_backward for callers that cannot call cudaMalloc -- for
+ * example a renderer embedded in a host application that owns all device
+ * memory through its own pool and forbids allocations on its frame loop
+ * (cudaMalloc can synchronise the device and stall a frame), or a process
+ * whose device-memory budget is fixed before it starts.
+ *
+ * Same arguments, results and error behaviour as adop_render_backward,
+ * except:
+ *   - Its scratch (the per-pixel backward records and the pose/intrinsics
+ *     block partials) lives in one library-owned static device array of
+ *     ADOP_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
+ *     library keeps until the process exits.  Calls needing more (about
+ *     4 * (c + 3 rounded up to a multiple of 4) bytes per pyramid pixel,
+ *     summed over cameras) return ADOP_ERR_OUT_OF_MEMORY before launching.
+ *   - Every frame must carry the forward's kept state (key, count, acc);
+ *     re-rendering would need further scratch (ADOP_ERR_INVALID_ARG).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls share the array and it keeps the previous call's contents
+ *     (every call overwrites what it reads).  Calls that overlap on the GPU
+ *     (on different streams, or from different threads) race: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define ADOP_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_camera* cams, int32_t n_cam,
+                                         const adop_params* params, const adop_frame* frames,
+                                         const float* const* grad_image, float* grad_feat,
+                                         float* grad_xyz, float* grad_pose, float* grad_intr,
+                                         adop_stream stream);
+
 /* Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by a pair of CUDA events recorded on the launch's stream (a few
  * microseconds of host time per launch, no device synchronisation).

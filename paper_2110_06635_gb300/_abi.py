@@ -79,6 +79,7 @@ SIGNATURES = {
     "adop_render_backward": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ct.c_size_t, _P]),
     "adop_last_error": (ct.c_char_p, []),
     "adop_abi_version": (ct.c_int32, []),
+    "adop_render_backward_noalloc": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
     "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
 }
@@ -319,3 +320,23 @@ def adop_render_backward(points: Points, cams, params: Params, frames, grad_imag
     _check(lib.adop_render_backward(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr, _dev_ptr(grad_feat),
                                     _dev_ptr(grad_xyz), _dev_ptr(grad_pose), _dev_ptr(grad_intr), wp, wn,
                                     _stream_ptr(stream)))
+
+
+def adop_render_backward_noalloc(points: Points, cams, params: Params, frames, grad_images, grad_feat=None,
+                                 grad_xyz=None, grad_pose=None, grad_intr=None, stream=None, crf_luts=None):
+    """adop_render_backward without a workspace: the library's static scratch
+    array is used instead (for callers that may not allocate device memory).
+    Frames must carry the forward's kept state."""
+    lib = load()
+    ps, pr = points.struct(), params.struct()
+    arr = _cams_array(cams, crf_luts)
+    fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
+    L = params.levels
+    gptr = (ct.c_void_p * (len(cams) * L))()
+    for k in range(len(cams)):
+        for l in range(L):
+            g = grad_images[k][l] if grad_images is not None and grad_images[k] is not None else None
+            gptr[k * L + l] = _dev_ptr(g)
+    _check(lib.adop_render_backward_noalloc(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr,
+                                            _dev_ptr(grad_feat), _dev_ptr(grad_xyz), _dev_ptr(grad_pose),
+                                            _dev_ptr(grad_intr), _stream_ptr(stream)))

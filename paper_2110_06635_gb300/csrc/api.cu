@@ -303,6 +303,59 @@ adop_status render_chunk(const adop_points* pts, const adop_camera* cams, int k0
   return ADOP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// scratch of adop_render_backward_noalloc: one static device array
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace adop
+
+// File scope, as the entry point's contract states: every device that loads
+// the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ADOP_NOALLOC_SCRATCH_BYTES];
+
+namespace adop {
+namespace {
+
+// Device address of the static scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+adop_status noalloc_scratch(char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(ADOP_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<char*>(g_scratch_ptr[dev]);
+  return ADOP_OK;
+}
+
+// Scratch layout of the no-allocation backward: records of every camera,
+// then the block partials of one launch chunk.
+WsLayout noalloc_layout(const adop_points* pts, const adop_camera* cams, int32_t n_cam, const adop_params* prm) {
+  WsLayout L{};
+  size_t o = 0;
+  for (int k = 0; k < n_cam; ++k) {
+    const int64_t px = pyramid_pixels(cams[k].K.w, cams[k].K.h, prm->levels, nullptr);
+    L.rec[k] = o;
+    o = align_up(o + (size_t)px * rec_stride(pts->c) * 4);
+  }
+  L.partials = o;
+  const int chunk = n_cam < kMaxCamsPerLaunch ? n_cam : kMaxCamsPerLaunch;
+  o = align_up(o + (size_t)chunk * kMaxPartialBlocks * 12 * 4);
+  L.total = o;
+  return L;
+}
+
 }  // namespace
 }  // namespace adop
 
@@ -454,6 +507,71 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
                         return launch_bwd_reduce(b.partials, nc, bx, grad_pose ? grad_pose + 6 * k0 : nullptr,
                                                  grad_intr ? grad_intr + 6 * k0 : nullptr, s);
                       })) != cudaSuccess)
+      return cuda_fail(e, "backward reduce launch");
+  }
+  g_last_error.clear();
+  return ADOP_OK;
+}
+
+adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_camera* cams, int32_t n_cam,
+                                         const adop_params* params, const adop_frame* frames,
+                                         const float* const* grad_image, float* grad_feat, float* grad_xyz,
+                                         float* grad_pose, float* grad_intr, adop_stream stream) {
+  adop_status st;
+  if ((st = validate_common(pts, cams, n_cam, params)) != ADOP_OK) return st;
+  if ((st = validate_frames(frames, n_cam, params, false)) != ADOP_OK) return st;
+  for (int k = 0; k < n_cam; ++k)
+    if (state_given(frames[k], params->levels) != 1)
+      return fail(ADOP_ERR_INVALID_ARG,
+                  "camera %d: the no-allocation backward needs the forward's kept key/count/acc", k);
+  const WsLayout L = noalloc_layout(pts, cams, n_cam, params);
+  if (L.total > ADOP_NOALLOC_SCRATCH_BYTES)
+    return fail(ADOP_ERR_OUT_OF_MEMORY,
+                "the no-allocation backward needs %zu bytes of scratch, its static array holds %zu; "
+                "use adop_render_backward with a workspace",
+                L.total, (size_t)ADOP_NOALLOC_SCRATCH_BYTES);
+  if (pts->n > 0 && grad_feat && ((uintptr_t)grad_feat & 15) != 0)
+    return fail(ADOP_ERR_INVALID_ARG, "grad_feat must be 16-byte aligned");
+  if (pts->n > 0 && grad_xyz && ((uintptr_t)grad_xyz & 3) != 0)
+    return fail(ADOP_ERR_INVALID_ARG, "grad_xyz must be 4-byte aligned");
+  char* ws = nullptr;
+  if ((st = noalloc_scratch(&ws)) != ADOP_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool assign = (params->flags & ADOP_FLAG_GRAD_ASSIGN) != 0;
+  const int mode = (n_cam == 1) ? (assign ? kGradAssign : kGradAccumulate) : kGradAtomic;
+  cudaError_t e;
+  if (assign && n_cam > 1 && pts->n > 0) {
+    if (grad_feat && (e = cudaMemsetAsync(grad_feat, 0, (size_t)pts->n * pts->c * 4, s)) != cudaSuccess)
+      return cuda_fail(e, "clear grad_feat");
+    if (grad_xyz && (e = cudaMemsetAsync(grad_xyz, 0, (size_t)pts->n * 12, s)) != cudaSuccess)
+      return cuda_fail(e, "clear grad_xyz");
+  }
+  const bool want_pose = grad_pose || grad_intr;
+  for (int k0 = 0; k0 < n_cam; k0 += kMaxCamsPerLaunch) {
+    const int nc = (n_cam - k0) < kMaxCamsPerLaunch ? (n_cam - k0) : kMaxCamsPerLaunch;
+    LaunchCams lc;
+    for (int j = 0; j < nc; ++j) {
+      const int k = k0 + j;
+      fill_cam(lc.c[j], cams[k], &frames[k], true, L, k, ws, pts, params);
+      for (int l = 0; l < params->levels; ++l) {
+        lc.c[j].grad[l] = grad_image ? grad_image[k * params->levels + l] : nullptr;
+        lc.c[j].image[l] = nullptr;
+      }
+    }
+    const PointArgs a = point_args(pts, params, nc);
+    if ((e = launch_bwd_prepass(lc, a, pts->c, s)) != cudaSuccess) return cuda_fail(e, "backward prepass launch");
+    if (pts->n == 0) continue;
+    const int bx = point_blocks(pts->n, nc) < kMaxPartialBlocks ? point_blocks(pts->n, nc) : kMaxPartialBlocks;
+    BwdArgs b{};
+    b.grad_feat = grad_feat;
+    b.grad_xyz = grad_xyz;
+    b.partials = want_pose ? reinterpret_cast<float*>(ws + L.partials) : nullptr;
+    b.mode = mode;
+    b.all_projected = (params->flags & ADOP_FLAG_GRAD_ALL_PROJECTED) ? 1 : 0;
+    if ((e = launch_bwd_points(lc, a, b, pts->c, pts->feat_dtype, bx, s)) != cudaSuccess)
+      return cuda_fail(e, "backward point pass launch");
+    if (want_pose && (e = launch_bwd_reduce(b.partials, nc, bx, grad_pose ? grad_pose + 6 * k0 : nullptr,
+                                            grad_intr ? grad_intr + 6 * k0 : nullptr, s)) != cudaSuccess)
       return cuda_fail(e, "backward reduce launch");
   }
   g_last_error.clear();
