@@ -198,14 +198,14 @@ def measured_peaks():
 def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: int) -> int:
     """Compulsory HBM bytes of one launch: every input read once, every output
     written once (per camera; n points, px pyramid pixels, c channels)."""
-    rs = ((c + 3) + 3) // 4 * 4
+    gs = c if c <= 2 else (c + 3) // 4 * 4
     return {
         "clear": px * (8 + 4 + 4 * c),                          # write key, count, sums
         "depth": n * 12 + px * 8 * 2,                           # read xyz; read+write keys
-        "accumulate": n * (12 + c * s_feat) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau; keys; RMW count+sums
+        "accumulate": n * (12 + c * s_feat + 1) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
-        "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 4 * rs),   # key, count, sums, G -> records
-        "bwd_points": n * (12 + c * s_feat + 4 * c + 12) + px * 4 * rs,  # xyz, tau -> dtau, dx; records
+        "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
+        "bwd_points": n * (1 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # mask, xyz, tau -> dtau, dx
         "bwd_reduce": 0,
     }[kernel]
 
@@ -232,7 +232,7 @@ class Workload:
         self.out_dtype = tdt
         self.pts = adop.Points(self.xyz, self.feat)
         self.params = adop.Params(LEVELS, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
-        self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device)
+        self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device, self.n)
         self.ws = adop.alloc_workspace(self.pts, [cam], self.params, None, device)
         G = scenes.upstream_grad(cam.w, cam.h, LEVELS, self.c, 2024)
         self.G_host = G

@@ -128,12 +128,18 @@ typedef struct {
  * that the backward pass re-uses.  Either all of key/count/acc are given
  * (the forward fills them; the backward reads them) or all are NULL (the
  * forward keeps them in the workspace; the backward re-renders them there,
- * as the paper's backward pass does). */
+ * as the paper's backward pass does).
+ * vis (optional, n bytes, only with key/count/acc): per point, bit l is set
+ * iff the point passed the fuzzy depth test at its layer-l pixel, i.e. is in
+ * Lambda of that pixel.  The forward writes it; the backward then skips the
+ * layers where a point is not in Lambda without looking at any pixel.  It is
+ * the result of the same FP32 comparisons, so results do not change. */
 typedef struct {
     void* image[ADOP_MAX_LEVELS];
     uint64_t* key[ADOP_MAX_LEVELS];
     uint32_t* count[ADOP_MAX_LEVELS];
     float* acc;
+    uint8_t* vis;
     adop_dtype out_dtype;
 } adop_frame;
 
@@ -194,9 +200,9 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
  *   - Its scratch (the per-pixel backward records and the pose/intrinsics
  *     block partials) lives in one library-owned static device array of
  *     ADOP_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
- *     library keeps until the process exits.  Calls needing more (about
- *     4 * (c + 3 rounded up to a multiple of 4) bytes per pyramid pixel,
- *     summed over cameras) return ADOP_ERR_OUT_OF_MEMORY before launching.
+ *     library keeps until the process exits.  Calls needing more (16 + 4 * c'
+ *     bytes per pyramid pixel, c' = c rounded up to a multiple of 4 from 3
+ *     on, summed over cameras) return ADOP_ERR_OUT_OF_MEMORY before launching.
  *   - Every frame must carry the forward's kept state (key, count, acc);
  *     re-rendering would need further scratch (ADOP_ERR_INVALID_ARG).
  *   - The first call on a device looks up the array's device address

@@ -62,7 +62,8 @@ class adop_params(ct.Structure):
 
 class adop_frame(ct.Structure):
     _fields_ = [("image", ct.c_void_p * ADOP_MAX_LEVELS), ("key", ct.c_void_p * ADOP_MAX_LEVELS),
-                ("count", ct.c_void_p * ADOP_MAX_LEVELS), ("acc", ct.c_void_p), ("out_dtype", ct.c_int32)]
+                ("count", ct.c_void_p * ADOP_MAX_LEVELS), ("acc", ct.c_void_p), ("vis", ct.c_void_p),
+                ("out_dtype", ct.c_int32)]
 
 
 class adop_kernel_stat(ct.Structure):
@@ -194,13 +195,17 @@ class Frame:
     key: object = None     # int64 (bit pattern of uint64), all layers concatenated
     count: object = None   # int32 (bit pattern of uint32)
     acc: object = None     # float32, pixel-major sums
+    vis: object = None     # uint8 per point: layers where the point is in Lambda
     w: int = 0
     h: int = 0
     levels: int = 0
     keep: list = field(default_factory=list)
 
     @staticmethod
-    def alloc(cam, c: int, levels: int, out_dtype=None, keep_state: bool = True, device="cuda"):
+    def alloc(cam, c: int, levels: int, out_dtype=None, keep_state: bool = True, device="cuda",
+              n_points: int | None = None):
+        """Images of every layer; with keep_state also key/count/acc, and the
+        per-point layer mask if n_points is given."""
         torch = _torch()
         out_dtype = out_dtype or torch.float32
         w, h = int(cam.w), int(cam.h)
@@ -211,6 +216,8 @@ class Frame:
             f.key = torch.empty(px, dtype=torch.int64, device=device)
             f.count = torch.empty(px, dtype=torch.int32, device=device)
             f.acc = torch.empty(px * c, dtype=torch.float32, device=device)
+            if n_points is not None:
+                f.vis = torch.empty(max(1, n_points), dtype=torch.uint8, device=device)
         return f
 
     def layer(self, buf, l):
@@ -227,6 +234,7 @@ class Frame:
                 fr.key[l] = self.key.data_ptr() + 8 * off[l]
                 fr.count[l] = self.count.data_ptr() + 4 * off[l]
             fr.acc = self.acc.data_ptr()
+            fr.vis = None if self.vis is None else self.vis.data_ptr()
         fr.out_dtype = dtype_code(self.images[0].dtype) if self.images else ADOP_F32
         return fr
 

@@ -31,8 +31,10 @@ struct DevCam {
   uint32_t* cnt[ADOP_MAX_LEVELS];
   void* image[ADOP_MAX_LEVELS];
   const float* grad[ADOP_MAX_LEVELS];
-  float* acc;  // pixel-major FP32 sums, c floats per pixel
-  float* rec;  // backward records, kRecStride(c) floats per pixel
+  float* acc;    // pixel-major FP32 sums, c floats per pixel
+  float* info;   // backward: per pixel {z_min, |Lambda|, <G, I>, 0}
+  float* gpm;    // backward: upstream gradient, pixel-major, g_stride(c) floats per pixel
+  uint8_t* vis;  // per point: bit l set iff the point is in Lambda of its layer-l pixel (or NULL)
   // photometric epilogue (Sec. 3.3); ev_scale = 2^-EV, computed on the host
   int32_t epi;
   int32_t crf_n;
@@ -47,9 +49,30 @@ struct LaunchCams {
   DevCam c[kMaxCamsPerLaunch];
 };
 
-// Backward record of a pixel: [min_z, |Lambda|, <G, I>, G_0 .. G_{c-1}], padded
-// to a multiple of 4 floats so that each record starts on 16 bytes.
-__host__ __device__ constexpr int rec_stride(int c) { return ((c + 3) + 3) / 4 * 4; }
+// Floats per pixel of the pixel-major upstream gradient: c, padded to a
+// multiple of 4 from c = 3 on so that every pixel starts on 16 bytes.
+__host__ __device__ constexpr int g_stride(int c) { return c <= 2 ? c : (c + 3) / 4 * 4; }
+
+// Load n floats (n a multiple of 4, 2, or 1) from a suitably aligned address.
+template <int N>
+__device__ __forceinline__ void load_vec(const float* __restrict__ src, float* dst) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 4; ++v) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(src) + v);
+      dst[4 * v] = q.x; dst[4 * v + 1] = q.y; dst[4 * v + 2] = q.z; dst[4 * v + 3] = q.w;
+    }
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 2; ++v) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(src) + v);
+      dst[2 * v] = q.x; dst[2 * v + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[k] = __ldg(src + k);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // FP32 projection contract

@@ -96,10 +96,12 @@ int64_t pyramid_pixels(int32_t w, int32_t h, int levels, int64_t* off) {
 
 bool finite(float v) { return std::isfinite(v); }
 
-// Workspace: per camera [keys | counts | sums | backward records], then the
-// pose/intrinsics block partials.
+// Workspace: per camera [keys | counts | sums | point layer masks | backward
+// pixel info | pixel-major upstream gradient], then the pose/intrinsics block
+// partials.
 struct WsLayout {
-  size_t key[ADOP_MAX_CAMERAS], cnt[ADOP_MAX_CAMERAS], acc[ADOP_MAX_CAMERAS], rec[ADOP_MAX_CAMERAS];
+  size_t key[ADOP_MAX_CAMERAS], cnt[ADOP_MAX_CAMERAS], acc[ADOP_MAX_CAMERAS], vis[ADOP_MAX_CAMERAS];
+  size_t info[ADOP_MAX_CAMERAS], gpm[ADOP_MAX_CAMERAS];
   size_t partials;
   size_t total;
 };
@@ -116,8 +118,12 @@ WsLayout layout(const adop_points* pts, const adop_camera* cams, int32_t n_cam, 
     o = align_up(o + (size_t)px * 4);
     L.acc[k] = o;
     o = align_up(o + (size_t)px * c * 4);
-    L.rec[k] = o;
-    o = align_up(o + (size_t)px * rec_stride(c) * 4);
+    L.vis[k] = o;
+    o = align_up(o + (size_t)pts->n);
+    L.info[k] = o;
+    o = align_up(o + (size_t)px * 16);
+    L.gpm[k] = o;
+    o = align_up(o + (size_t)px * g_stride(c) * 4);
   }
   L.partials = o;
   o = align_up(o + (size_t)n_cam * kMaxPartialBlocks * 12 * 4);
@@ -197,6 +203,8 @@ adop_status validate_frames(const adop_frame* frames, int32_t n_cam, const adop_
     if (sg < 0) return fail(ADOP_ERR_INVALID_ARG, "camera %d: key/count/acc must be all set or all NULL", k);
     if (sg == 1 && ((uintptr_t)f.acc & 15) != 0)
       return fail(ADOP_ERR_INVALID_ARG, "camera %d: acc must be 16-byte aligned", k);
+    if (sg == 0 && f.vis)
+      return fail(ADOP_ERR_INVALID_ARG, "camera %d: vis needs key/count/acc", k);
     if (sg == 1)
       for (int l = 0; l < prm->levels; ++l)
         if (((uintptr_t)f.key[l] & 7) != 0 || ((uintptr_t)f.count[l] & 3) != 0)
@@ -238,7 +246,9 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
     d.image[l] = f ? f->image[l] : nullptr;
   }
   d.acc = use_frame_state ? f->acc : reinterpret_cast<float*>(ws + L.acc[k]);
-  d.rec = reinterpret_cast<float*>(ws + L.rec[k]);
+  d.vis = use_frame_state ? f->vis : reinterpret_cast<uint8_t*>(ws + L.vis[k]);
+  d.info = reinterpret_cast<float*>(ws + L.info[k]);
+  d.gpm = reinterpret_cast<float*>(ws + L.gpm[k]);
   const adop_photometric& ph = cam.ph;
   d.epi = ((prm->flags & ADOP_FLAG_EPILOGUE) && ph.enabled) ? 1 : 0;
   d.ev_scale = (float)std::exp2(-(double)ph.ev);
@@ -346,8 +356,10 @@ WsLayout noalloc_layout(const adop_points* pts, const adop_camera* cams, int32_t
   size_t o = 0;
   for (int k = 0; k < n_cam; ++k) {
     const int64_t px = pyramid_pixels(cams[k].K.w, cams[k].K.h, prm->levels, nullptr);
-    L.rec[k] = o;
-    o = align_up(o + (size_t)px * rec_stride(pts->c) * 4);
+    L.info[k] = o;
+    o = align_up(o + (size_t)px * 16);
+    L.gpm[k] = o;
+    o = align_up(o + (size_t)px * g_stride(pts->c) * 4);
   }
   L.partials = o;
   const int chunk = n_cam < kMaxCamsPerLaunch ? n_cam : kMaxCamsPerLaunch;

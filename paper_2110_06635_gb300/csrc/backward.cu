@@ -4,15 +4,20 @@
 // SE(3) tangent of the pose (Eq. tangent) and the intrinsics (Eq. partial).
 //
 //   k_bwd_prepass  one thread per pixel: packs what a point needs to know
-//                  about a pixel into one record -- min depth, |Lambda|,
-//                  <G, I> and the (epilogue-chained) upstream gradient G --
-//                  so that the 5 pixels a point visits per layer cost 5
-//                  contiguous record reads instead of 2c strided gathers.
-//   k_bwd_points   one thread per point and camera: visits its pixel and the
-//                  4 neighbours in every layer, writes its own dL/dtau and
+//                  about a pixel -- min depth, |Lambda|, <G, I> in one 16-byte
+//                  record, and the (epilogue-chained) upstream gradient G
+//                  pixel-major -- so that the pixels a point visits cost one
+//                  16-byte read each, plus one contiguous G read only where
+//                  the induced change is non-zero.
+//   k_bwd_points   one thread per point and camera: visits, in every layer
+//                  where the accumulate pass recorded the point in Lambda, its
+//                  pixel and the 4 neighbours; writes its own dL/dtau and
 //                  dL/dx (owner computes: no atomics for one camera), and
 //                  reduces pose/intrinsic terms warp -> block into per-block
 //                  partial sums.
+//   k_bwd_items    the same when the forward recorded each point's layer
+//                  mask: warps compact their (point, layer) pairs in shared
+//                  memory and process them densely.
 //   k_bwd_reduce   sums the block partials in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
@@ -23,7 +28,7 @@ namespace adop {
 template <int C>
 __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant__ LaunchCams cams,
                                                           const __grid_constant__ PointArgs a) {
-  constexpr int RS = rec_stride(C);
+  constexpr int GS = g_stride(C);
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -33,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const int64_t np = cam.off[l + 1] - cam.off[l];
     const uint32_t n = cam.cnt[l][p];
     const unsigned long long key = cam.key[l][p];
-    float I[C], G[C];
+    float I[C], G[GS];
     if (n == 0) {
 #pragma unroll
       for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
@@ -45,6 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const float* gl = cam.grad[l];
 #pragma unroll
     for (int k = 0; k < C; ++k) G[k] = gl ? __ldg(gl + k * np + p) : 0.0f;
+#pragma unroll
+    for (int k = C; k < GS; ++k) G[k] = 0.0f;
     if (l == 0 && cam.epi) {
       const int32_t pu = (int32_t)(p % cam.w), pv = (int32_t)(p / cam.w);
 #pragma unroll
@@ -57,179 +64,104 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     float gi = 0.0f;
 #pragma unroll
     for (int k = 0; k < C; ++k) gi = fmaf(G[k], I[k], gi);
-    float r[RS];
-    r[0] = __uint_as_float((uint32_t)(key >> 32));
-    r[1] = (float)n;
-    r[2] = gi;
+    reinterpret_cast<float4*>(cam.info)[g] =
+        make_float4(__uint_as_float((uint32_t)(key >> 32)), (float)n, gi, 0.0f);
+    float* dst = cam.gpm + g * GS;
+    if constexpr (GS % 4 == 0) {
 #pragma unroll
-    for (int k = 0; k < C; ++k) r[3 + k] = G[k];
+      for (int v = 0; v < GS / 4; ++v)
+        reinterpret_cast<float4*>(dst)[v] = make_float4(G[4 * v], G[4 * v + 1], G[4 * v + 2], G[4 * v + 3]);
+    } else {
 #pragma unroll
-    for (int k = 3 + C; k < RS; ++k) r[k] = 0.0f;
-    float4* dst = reinterpret_cast<float4*>(cam.rec + g * RS);
-#pragma unroll
-    for (int v = 0; v < RS / 4; ++v) dst[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+      for (int k = 0; k < GS; ++k) dst[k] = G[k];
+    }
   }
 }
 
-template <int RS>
-__device__ __forceinline__ void load_rec(const float* rp, float (&r)[RS]) {
-#pragma unroll
-  for (int v = 0; v < RS / 4; ++v) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(rp) + v);
-    r[4 * v] = q.x;
-    r[4 * v + 1] = q.y;
-    r[4 * v + 2] = q.z;
-    r[4 * v + 3] = q.w;
-  }
+// Chain rule from the layer-0 pixel gradient (du0, dv0) to the camera-space
+// point, the pose tangent (left increment exp(xi)(R,t): dX/dnu = I,
+// dX/domega = -[X]x), the intrinsics (fx, fy, cx, cy, k1, k2) and the world
+// position (dL/dx = R^T dL/dX).  FP32.
+__device__ __forceinline__ void chain_rule(const DevCam& cam, float X0, float X1, float X2, float du0, float dv0,
+                                           float (&red)[12], float (&gx)[3]) {
+  const float iz = 1.0f / X2;
+  const float xn = X0 * iz, yn = X1 * iz;
+  const float r2 = xn * xn + yn * yn;
+  const float d = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
+  const float dd = cam.k1 + r2 * (2.0f * cam.k2 + 3.0f * cam.k3 * r2);
+  const float xd = xn * d + 2.0f * cam.p1 * xn * yn + cam.p2 * (r2 + 2.0f * xn * xn);
+  const float yd = yn * d + cam.p1 * (r2 + 2.0f * yn * yn) + 2.0f * cam.p2 * xn * yn;
+  const float cross = 2.0f * xn * yn * dd + 2.0f * cam.p1 * xn + 2.0f * cam.p2 * yn;
+  const float dxd_dxn = d + 2.0f * xn * xn * dd + 2.0f * cam.p1 * yn + 6.0f * cam.p2 * xn;
+  const float dyd_dyn = d + 2.0f * yn * yn * dd + 6.0f * cam.p1 * yn + 2.0f * cam.p2 * xn;
+  const float gxd = cam.fx * du0, gyd = cam.fy * dv0;
+  const float gxn = gxd * dxd_dxn + gyd * cross;
+  const float gyn = gxd * cross + gyd * dyd_dyn;
+  const float dX0 = gxn * iz, dX1 = gyn * iz, dX2 = -(gxn * xn + gyn * yn) * iz;
+  red[0] += dX0;
+  red[1] += dX1;
+  red[2] += dX2;
+  red[3] += X1 * dX2 - X2 * dX1;
+  red[4] += X2 * dX0 - X0 * dX2;
+  red[5] += X0 * dX1 - X1 * dX0;
+  red[6] += du0 * xd;
+  red[7] += dv0 * yd;
+  red[8] += du0;
+  red[9] += dv0;
+  red[10] += (gxd * xn + gyd * yn) * r2;
+  red[11] += (gxd * xn + gyd * yn) * r2 * r2;
+  gx[0] = cam.R[0] * dX0 + cam.R[3] * dX1 + cam.R[6] * dX2;
+  gx[1] = cam.R[1] * dX0 + cam.R[4] * dX1 + cam.R[7] * dX2;
+  gx[2] = cam.R[2] * dX0 + cam.R[5] * dX1 + cam.R[8] * dX2;
 }
 
-template <int C, typename TF>
-__global__ void __launch_bounds__(kThreads) k_bwd_points(const __grid_constant__ LaunchCams cams,
-                                                         const __grid_constant__ PointArgs a,
-                                                         const __grid_constant__ BwdArgs b) {
-  constexpr int RS = rec_stride(C);
-  const DevCam& cam = cams.c[blockIdx.y];
-  const TF* feat = reinterpret_cast<const TF*>(a.feat);
-  float red[12];
+// Write one point's dL/dtau and dL/dx: overwrite (streaming stores),
+// accumulate (owner computes) or add atomically (several cameras).
+template <int C>
+__device__ __forceinline__ void write_point_grads(const BwdArgs& b, int64_t i, const float (&gf)[C],
+                                                  const float (&gx)[3], bool touched) {
+  if (b.mode == kGradAssign) {
+    if (b.grad_feat) {
+      float* dst = b.grad_feat + i * C;
+      if constexpr (C % 4 == 0) {
 #pragma unroll
-  for (int k = 0; k < 12; ++k) red[k] = 0.0f;
-
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    float gf[C];
+        for (int v = 0; v < C / 4; ++v)
+          __stcs(reinterpret_cast<float4*>(dst) + v, make_float4(gf[4 * v], gf[4 * v + 1], gf[4 * v + 2], gf[4 * v + 3]));
+      } else {
 #pragma unroll
-    for (int k = 0; k < C; ++k) gf[k] = 0.0f;
-    float gx[3] = {0.0f, 0.0f, 0.0f};
-    bool touched = false;
-
-    float X0, X1, X2, u0, v0;
-    transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-    const bool valid = (X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2));
-    if (valid) {
-      camera(cam, X0, X1, X2, u0, v0);
-      float tau[C];
-      bool loaded = false;
-      float du0 = 0.0f, dv0 = 0.0f;
-      bool spatial = false;
-      for (int l = 0; l < a.levels; ++l) {
-        int32_t pu, pv;
-        if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
-        const int32_t wl = cam.w >> l, hl = cam.h >> l;
-        const float* base = cam.rec + cam.off[l] * RS;
-        float rp[RS];
-        load_rec<RS>(base + ((int64_t)pv * wl + pu) * RS, rp);
-        const bool vis = X2 <= __fmul_rn(rp[0], a.a1);
-        if (vis) {
-          // dI(p)/dtau_i = 1/|Lambda(p)| for every member of Lambda(p)
-#pragma unroll
-          for (int k = 0; k < C; ++k) gf[k] += __fdiv_rn(rp[3 + k], rp[1]);
-          touched = true;
-        }
-        if (!(vis || b.all_projected) || (b.grad_xyz == nullptr && b.partials == nullptr)) continue;
-        if (!loaded) {
-          load_feat<C, TF>(feat, i, tau);
-          loaded = true;
-        }
-        // induced change at the 4 neighbours (+u, -u, +v, -v), contracted with G there
-        float cq[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int32_t qu = pu + (s == 0 ? 1 : (s == 1 ? -1 : 0));
-          const int32_t qv = pv + (s == 2 ? 1 : (s == 3 ? -1 : 0));
-          cq[s] = 0.0f;
-          if (qu < 0 || qu >= wl || qv < 0 || qv >= hl) continue;
-          float rq[RS];
-          load_rec<RS>(base + ((int64_t)qv * wl + qu) * RS, rq);
-          float wgt;
-          if (rq[1] == 0.0f) wgt = 1.0f;                              // empty: overwrite background
-          else if (X2 > __fmul_rn(rq[0], a.a1)) wgt = 0.0f;          // behind the target surface
-          else if (__fmul_rn(X2, a.a1) < rq[0]) wgt = 1.0f;          // in front: replaces the mean
-          else wgt = __frcp_rn(1.0f + rq[1]);                         // joins the fuzzy blend
-          if (wgt == 0.0f) continue;
-          float dot = 0.0f;
-#pragma unroll
-          for (int k = 0; k < C; ++k) dot = fmaf(rq[3 + k], tau[k], dot);
-          cq[s] = wgt * (dot - rq[2]);
-        }
-        const float s = layer_scale(l);
-        du0 = fmaf(0.5f * (cq[0] - cq[1]), s, du0);
-        dv0 = fmaf(0.5f * (cq[2] - cq[3]), s, dv0);
-        spatial = true;
-      }
-      if (spatial && (du0 != 0.0f || dv0 != 0.0f)) {
-        // chain rule through the camera model (FP32)
-        const float iz = 1.0f / X2;
-        const float xn = X0 * iz, yn = X1 * iz;
-        const float r2 = xn * xn + yn * yn;
-        const float d = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
-        const float dd = cam.k1 + r2 * (2.0f * cam.k2 + 3.0f * cam.k3 * r2);
-        const float xd = xn * d + 2.0f * cam.p1 * xn * yn + cam.p2 * (r2 + 2.0f * xn * xn);
-        const float yd = yn * d + cam.p1 * (r2 + 2.0f * yn * yn) + 2.0f * cam.p2 * xn * yn;
-        const float cross = 2.0f * xn * yn * dd + 2.0f * cam.p1 * xn + 2.0f * cam.p2 * yn;
-        const float dxd_dxn = d + 2.0f * xn * xn * dd + 2.0f * cam.p1 * yn + 6.0f * cam.p2 * xn;
-        const float dyd_dyn = d + 2.0f * yn * yn * dd + 6.0f * cam.p1 * yn + 2.0f * cam.p2 * xn;
-        const float gxd = cam.fx * du0, gyd = cam.fy * dv0;
-        const float gxn = gxd * dxd_dxn + gyd * cross;
-        const float gyn = gxd * cross + gyd * dyd_dyn;
-        const float dX0 = gxn * iz, dX1 = gyn * iz, dX2 = -(gxn * xn + gyn * yn) * iz;
-        // left increment exp(xi) (R, t): dX/dnu = I, dX/domega = -[X]x
-        red[0] += dX0;
-        red[1] += dX1;
-        red[2] += dX2;
-        red[3] += X1 * dX2 - X2 * dX1;
-        red[4] += X2 * dX0 - X0 * dX2;
-        red[5] += X0 * dX1 - X1 * dX0;
-        // intrinsics fx, fy, cx, cy, k1, k2
-        red[6] += du0 * xd;
-        red[7] += dv0 * yd;
-        red[8] += du0;
-        red[9] += dv0;
-        red[10] += (gxd * xn + gyd * yn) * r2;
-        red[11] += (gxd * xn + gyd * yn) * r2 * r2;
-        // dL/dx = R^T dL/dX
-        gx[0] = cam.R[0] * dX0 + cam.R[3] * dX1 + cam.R[6] * dX2;
-        gx[1] = cam.R[1] * dX0 + cam.R[4] * dX1 + cam.R[7] * dX2;
-        gx[2] = cam.R[2] * dX0 + cam.R[5] * dX1 + cam.R[8] * dX2;
-        touched = true;
+        for (int k = 0; k < C; ++k) __stcs(dst + k, gf[k]);
       }
     }
-
-    // write this point's gradients
-    if (b.mode == kGradAssign) {
+    if (b.grad_xyz) {
+      __stcs(b.grad_xyz + 3 * i, gx[0]);
+      __stcs(b.grad_xyz + 3 * i + 1, gx[1]);
+      __stcs(b.grad_xyz + 3 * i + 2, gx[2]);
+    }
+  } else if (touched) {
+    if (b.mode == kGradAccumulate) {
       if (b.grad_feat) {
         float* dst = b.grad_feat + i * C;
 #pragma unroll
-        for (int k = 0; k < C; ++k) dst[k] = gf[k];
+        for (int k = 0; k < C; ++k) dst[k] += gf[k];
       }
       if (b.grad_xyz) {
-        b.grad_xyz[3 * i] = gx[0];
-        b.grad_xyz[3 * i + 1] = gx[1];
-        b.grad_xyz[3 * i + 2] = gx[2];
+        b.grad_xyz[3 * i] += gx[0];
+        b.grad_xyz[3 * i + 1] += gx[1];
+        b.grad_xyz[3 * i + 2] += gx[2];
       }
-    } else if (touched) {
-      if (b.mode == kGradAccumulate) {
-        if (b.grad_feat) {
-          float* dst = b.grad_feat + i * C;
-#pragma unroll
-          for (int k = 0; k < C; ++k) dst[k] += gf[k];
-        }
-        if (b.grad_xyz) {
-          b.grad_xyz[3 * i] += gx[0];
-          b.grad_xyz[3 * i + 1] += gx[1];
-          b.grad_xyz[3 * i + 2] += gx[2];
-        }
-      } else {
-        if (b.grad_feat) atomic_add_vec<C>(b.grad_feat + i * C, gf);
-        if (b.grad_xyz) {
-          atomicAdd(b.grad_xyz + 3 * i, gx[0]);
-          atomicAdd(b.grad_xyz + 3 * i + 1, gx[1]);
-          atomicAdd(b.grad_xyz + 3 * i + 2, gx[2]);
-        }
+    } else {
+      if (b.grad_feat) atomic_add_vec<C>(b.grad_feat + i * C, gf);
+      if (b.grad_xyz) {
+        atomicAdd(b.grad_xyz + 3 * i, gx[0]);
+        atomicAdd(b.grad_xyz + 3 * i + 1, gx[1]);
+        atomicAdd(b.grad_xyz + 3 * i + 2, gx[2]);
       }
     }
   }
+}
 
-  // pose / intrinsics: warp shuffle -> shared memory -> one partial per block
-  if (b.partials == nullptr) return;
+// Pose / intrinsics terms: warp shuffle -> shared memory -> one partial per block.
+__device__ __forceinline__ void block_partials(const BwdArgs& b, float (&red)[12]) {
   __shared__ float sm[kThreads / 32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -246,6 +178,225 @@ __global__ void __launch_bounds__(kThreads) k_bwd_points(const __grid_constant__
     for (int w = 0; w < kThreads / 32; ++w) v += sm[w][threadIdx.x];
     b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + threadIdx.x] = v;
   }
+}
+
+// Eq. spatialderiv at the 4 neighbours (+u, -u, +v, -v) of pixel (pu, pv) of a
+// layer whose records start at `base`, contracted with the upstream gradient
+// there; returns the layer-pixel gradients g_u, g_v of Eq. gradp.
+template <int C>
+__device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __restrict__ info, int64_t base,
+                                             int32_t pu, int32_t pv, int32_t wl, int32_t hl, float z, float a1,
+                                             const float* tau, float& g_u, float& g_v) {
+  constexpr int GS = g_stride(C);
+  float cq[4];
+  float4 iq[4];
+  int64_t gq[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {  // issue the 4 record loads together
+    const int32_t qu = pu + (s == 0 ? 1 : (s == 1 ? -1 : 0));
+    const int32_t qv = pv + (s == 2 ? 1 : (s == 3 ? -1 : 0));
+    gq[s] = (qu < 0 || qu >= wl || qv < 0 || qv >= hl) ? -1 : base + (int64_t)qv * wl + qu;
+    iq[s] = gq[s] >= 0 ? __ldg(info + gq[s]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    cq[s] = 0.0f;
+    if (gq[s] < 0) continue;
+    float wgt;
+    if (iq[s].y == 0.0f) wgt = 1.0f;                            // empty: overwrite background
+    else if (z > __fmul_rn(iq[s].x, a1)) wgt = 0.0f;            // behind the target surface
+    else if (__fmul_rn(z, a1) < iq[s].x) wgt = 1.0f;            // in front: replaces the mean
+    else wgt = __frcp_rn(1.0f + iq[s].y);                        // joins the fuzzy blend
+    if (wgt == 0.0f) continue;
+    float G[GS];
+    load_vec<GS>(cam.gpm + gq[s] * GS, G);
+    float dot = 0.0f;
+#pragma unroll
+    for (int k = 0; k < C; ++k) dot = fmaf(G[k], tau[k], dot);
+    cq[s] = wgt * (dot - iq[s].z);
+  }
+  g_u = 0.5f * (cq[0] - cq[1]);
+  g_v = 0.5f * (cq[2] - cq[3]);
+}
+
+template <int C, typename TF>
+__global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constant__ LaunchCams cams,
+                                                            const __grid_constant__ PointArgs a,
+                                                            const __grid_constant__ BwdArgs b) {
+  constexpr int GS = g_stride(C);
+  const DevCam& cam = cams.c[blockIdx.y];
+  const TF* feat = reinterpret_cast<const TF*>(a.feat);
+  const float4* info = reinterpret_cast<const float4*>(cam.info);
+  const bool spatial_out = b.grad_xyz != nullptr || b.partials != nullptr;
+  float red[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) red[k] = 0.0f;
+
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float gf[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) gf[k] = 0.0f;
+    float gx[3] = {0.0f, 0.0f, 0.0f};
+    bool touched = false;
+    // layers in which the point is in Lambda of its pixel, as recorded by the
+    // accumulate pass; without the record every in-bounds layer is examined
+    const uint32_t vmask = cam.vis ? (uint32_t)cam.vis[i] : 0xFFu;
+    if (vmask != 0u || b.all_projected) {
+      float X0, X1, X2, u0, v0;
+      transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
+      const bool valid = (X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2));
+      if (valid) {
+        camera(cam, X0, X1, X2, u0, v0);
+        float tau[C];
+        bool loaded = false;
+        float du0 = 0.0f, dv0 = 0.0f;
+        bool spatial = false;
+        for (int l = 0; l < a.levels; ++l) {
+          if (!((vmask >> l) & 1u) && !b.all_projected) continue;
+          int32_t pu, pv;
+          if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
+          const int32_t wl = cam.w >> l, hl = cam.h >> l;
+          const int64_t base = cam.off[l];
+          const int64_t gp = base + (int64_t)pv * wl + pu;
+          const float4 ip = __ldg(info + gp);
+          const bool vis = cam.vis ? (((vmask >> l) & 1u) != 0u) : (X2 <= __fmul_rn(ip.x, a.a1));
+          if (vis) {
+            // dI(p)/dtau_i = 1/|Lambda(p)| for every member of Lambda(p)
+            float G[GS];
+            load_vec<GS>(cam.gpm + gp * GS, G);
+#pragma unroll
+            for (int k = 0; k < C; ++k) gf[k] += __fdiv_rn(G[k], ip.y);
+            touched = true;
+          }
+          if (!(vis || b.all_projected) || !spatial_out) continue;
+          if (!loaded) {
+            load_feat<C, TF>(feat, i, tau);
+            loaded = true;
+          }
+          float g_u, g_v;
+          spatial_grad<C>(cam, info, base, pu, pv, wl, hl, X2, a.a1, tau, g_u, g_v);
+          const float sc = layer_scale(l);
+          du0 = fmaf(g_u, sc, du0);
+          dv0 = fmaf(g_v, sc, dv0);
+          spatial = true;
+        }
+        if (spatial && (du0 != 0.0f || dv0 != 0.0f)) {
+          chain_rule(cam, X0, X1, X2, du0, dv0, red, gx);
+          touched = true;
+        }
+      }
+    }
+
+    write_point_grads<C>(b, i, gf, gx, touched);
+  }
+  if (b.partials != nullptr) block_partials(b, red);
+}
+
+// The same backward when the accumulate pass recorded each point's layer mask
+// (and only points in Lambda get spatial gradients).  Each warp takes 32
+// consecutive points, lists their (point, layer) pairs that are in Lambda in
+// shared memory and processes that list densely, one pair per lane, so that
+// lanes are not idle on the (majority of) occluded pairs.  Per-point sums
+// over layers go through shared-memory atomics; the owning lane then applies
+// the chain rule and writes its point's gradients.
+template <int C, typename TF>
+__global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant__ LaunchCams cams,
+                                                           const __grid_constant__ PointArgs a,
+                                                           const __grid_constant__ BwdArgs b) {
+  constexpr int GS = g_stride(C);
+  constexpr int PS = (3 + C) | 1;  // per point: z, u0, v0, tau (odd stride: no bank conflicts)
+  constexpr int AS = (C + 2) | 1;  // per point: sum of G/|Lambda|, du0, dv0
+  constexpr int kWarps = kThreads / 32;
+  __shared__ float s_pt[kWarps][32 * PS];
+  __shared__ float s_acc[kWarps][32 * AS];
+  __shared__ uint8_t s_item[kWarps][32 * ADOP_MAX_LEVELS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const DevCam& cam = cams.c[blockIdx.y];
+  const TF* feat = reinterpret_cast<const TF*>(a.feat);
+  const float4* info = reinterpret_cast<const float4*>(cam.info);
+  const bool spatial_out = b.grad_xyz != nullptr || b.partials != nullptr;
+  float* pt = s_pt[warp];
+  float* acc = s_acc[warp];
+  uint8_t* item = s_item[warp];
+  float red[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) red[k] = 0.0f;
+
+  const int64_t stride = (int64_t)gridDim.x * kWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < a.n; base += stride) {
+    const int64_t i = base + lane;
+    const uint32_t mask = i < a.n ? (uint32_t)__ldcs(cam.vis + i) : 0u;
+    float X0 = 0.f, X1 = 0.f, X2 = 1.f;
+    if (mask) {
+      float u0, v0;
+      transform(cam, __ldcs(a.xyz + 3 * i), __ldcs(a.xyz + 3 * i + 1), __ldcs(a.xyz + 3 * i + 2), X0, X1, X2);
+      camera(cam, X0, X1, X2, u0, v0);
+      float tau[C];
+      load_feat<C, TF>(feat, i, tau);
+      pt[lane * PS + 0] = X2;
+      pt[lane * PS + 1] = u0;
+      pt[lane * PS + 2] = v0;
+#pragma unroll
+      for (int k = 0; k < C; ++k) pt[lane * PS + 3 + k] = tau[k];
+    }
+#pragma unroll
+    for (int k = 0; k < C + 2; ++k) acc[lane * AS + k] = 0.0f;
+    // list the pairs: exclusive scan of the per-lane pair counts
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int slot = incl - cnt;
+    for (uint32_t m = mask; m; m &= m - 1) item[slot++] = (uint8_t)((lane << 3) | (__ffs(m) - 1));
+    __syncwarp();
+    for (int r = 0; r < total; r += 32) {
+      const int k = r + lane;
+      if (k < total) {
+        const int it = item[k];
+        const int src = it >> 3, l = it & 7;
+        const float* sp = pt + src * PS;
+        const float z = sp[0];
+        int32_t pu, pv;
+        if (pixel_at(sp[1], sp[2], l, cam.w, cam.h, pu, pv)) {  // always true for a listed pair
+          const int32_t wl = cam.w >> l, hl = cam.h >> l;
+          const int64_t lb = cam.off[l];
+          const int64_t gp = lb + (int64_t)pv * wl + pu;
+          const float4 ip = __ldg(info + gp);
+          float G[GS];
+          load_vec<GS>(cam.gpm + gp * GS, G);
+          float* ap = acc + src * AS;
+#pragma unroll
+          for (int c = 0; c < C; ++c) atomicAdd(ap + c, __fdiv_rn(G[c], ip.y));
+          if (spatial_out) {
+            float tau[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) tau[c] = sp[3 + c];
+            float g_u, g_v;
+            spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, z, a.a1, tau, g_u, g_v);
+            const float sc = layer_scale(l);
+            atomicAdd(ap + C, g_u * sc);
+            atomicAdd(ap + C + 1, g_v * sc);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (i < a.n) {
+      float gf[C];
+#pragma unroll
+      for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k];
+      float gx[3] = {0.0f, 0.0f, 0.0f};
+      const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];
+      if (mask && (du0 != 0.0f || dv0 != 0.0f)) chain_rule(cam, X0, X1, X2, du0, dv0, red, gx);
+      write_point_grads<C>(b, i, gf, gx, mask != 0u);
+    }
+    __syncwarp();
+  }
+  if (b.partials != nullptr) block_partials(b, red);
 }
 
 // One block per camera, warp k sums element k over all block partials.
@@ -275,7 +426,13 @@ cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const 
                               adop_dtype fd, int blocks_x, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   const dim3 grid(blocks_x, a.ncam);
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_points<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  bool dense = !b.all_projected;
+  for (int k = 0; k < a.ncam; ++k) dense = dense && cams.c[k].vis != nullptr;
+  if (dense) {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  } else {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_points<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  }
   return cudaGetLastError();
 }
 

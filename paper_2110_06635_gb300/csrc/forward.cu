@@ -55,6 +55,10 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
 
 // ---------------------------------------------------------------------------
 // K1 depth pass: key[l][p] = min over points of (bits(z) << 32 | i)
+// One thread per point; the key is read first and the 64-bit atomicMin is
+// issued only if the point can still win (most points are occluded).
+// (Grouping lanes that share a pixel with __match_any_sync before the atomic
+// was measured 4x slower on GB300: the per-group warp intrinsics serialise.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
@@ -70,7 +74,6 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
       int32_t pu, pv;
       if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
       unsigned long long* slot = cam.key[l] + (int64_t)pv * (cam.w >> l) + pu;
-      // most points are occluded: read first, issue the atomic only if it can win
       if (key < __ldcg(slot)) atomicMin(slot, key);
     }
   }
@@ -78,7 +81,9 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
 
 // ---------------------------------------------------------------------------
 // K2 accumulate: points with z <= f32(z_min * (1 + alpha)) add their
-// descriptor to the pixel's FP32 sum and increment |Lambda|
+// descriptor to the pixel's FP32 sum (float4 vector atomics) and increment
+// |Lambda|; each point's layer mask of passed tests is written for the
+// backward pass.
 // ---------------------------------------------------------------------------
 template <int C, typename TF>
 __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ LaunchCams cams,
@@ -86,26 +91,29 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t mask = 0;  // bit l: the point is in Lambda of its layer-l pixel
     float X0, X1, X2, u0, v0;
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-    if (!(X2 > a.znear)) continue;
-    if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
-    camera(cam, X0, X1, X2, u0, v0);
-    float f[C];
-    bool loaded = false;
-    for (int l = 0; l < a.levels; ++l) {
-      int32_t pu, pv;
-      if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
-      const int64_t p = (int64_t)pv * (cam.w >> l) + pu;
-      const float minz = __uint_as_float((uint32_t)(__ldg(cam.key[l] + p) >> 32));
-      if (!(X2 <= __fmul_rn(minz, a.a1))) continue;
-      if (!loaded) {
-        load_feat<C, TF>(feat, i, f);
-        loaded = true;
+    if ((X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
+      camera(cam, X0, X1, X2, u0, v0);
+      float f[C];
+      bool loaded = false;
+      for (int l = 0; l < a.levels; ++l) {
+        int32_t pu, pv;
+        if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
+        const int64_t p = (int64_t)pv * (cam.w >> l) + pu;
+        const float minz = __uint_as_float((uint32_t)(__ldg(cam.key[l] + p) >> 32));
+        if (!(X2 <= __fmul_rn(minz, a.a1))) continue;
+        if (!loaded) {
+          load_feat<C, TF>(feat, i, f);
+          loaded = true;
+        }
+        atomic_add_vec<C>(cam.acc + (cam.off[l] + p) * C, f);
+        atomicAdd(cam.cnt[l] + p, 1u);
+        mask |= 1u << l;
       }
-      atomic_add_vec<C>(cam.acc + (cam.off[l] + p) * C, f);
-      atomicAdd(cam.cnt[l] + p, 1u);
     }
+    if (cam.vis) cam.vis[i] = (uint8_t)mask;
   }
 }
 

@@ -67,7 +67,7 @@ def to_np(t):
 
 def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, flags=0,
             grads=None, out_dtype="f32", keep_state=True, backward=True, normals=False, crf=True,
-            grad_assign=False, init=0.0):
+            grad_assign=False, init=0.0, vis=True):
     """Forward (+ backward) through the C ABI; returns numpy results."""
     import torch
     dev = "cuda"
@@ -81,7 +81,8 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
     params = adop.Params(levels, alpha, znear, bg, flags)
     luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(dev)
             if (crf and getattr(c, "crf", None) is not None) else None for c in cams]
-    frames = [adop.Frame.alloc(c, scene.c, levels, torch_dtype(out_dtype), keep_state, dev) for c in cams]
+    frames = [adop.Frame.alloc(c, scene.c, levels, torch_dtype(out_dtype), keep_state, dev,
+                               scene.n if vis else None) for c in cams]
     ws = adop.alloc_workspace(pts, cams, params, luts, dev)
     adop.adop_render_forward(pts, cams, params, frames, ws, crf_luts=luts)
     out = {"frames": frames}

@@ -61,6 +61,17 @@ def test_recompute_matches_kept_state(adop, orc, tiny):
     compare(g, r, check_state=False)
 
 
+def test_without_visibility_mask(adop, orc, tiny):
+    """Kept state without the per-point layer mask: the backward takes the
+    fuzzy decision from the pixel records instead, with the same results."""
+    sc, cams = tiny
+    G = _grads(cams, sc.c, 4, 7)
+    for flags in (0, adop.ADOP_FLAG_GRAD_ALL_PROJECTED):
+        g = gpu_run(adop, sc, cams, "f32", grads=G, vis=False, flags=flags)
+        r = oracle_run(orc, sc, cams, "f32", grads=G, all_projected=bool(flags))
+        compare(g, r)
+
+
 def test_accumulate_and_assign(adop, orc, tiny):
     sc, cams = tiny
     G = _grads(cams, sc.c, 4, 7)
