@@ -221,6 +221,69 @@ adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_came
                                          float* grad_xyz, float* grad_pose, float* grad_intr,
                                          adop_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Render server: continuous batching of forward renders.
+ *
+ * A server keeps point clouds resident (it borrows their device pointers,
+ * which must stay valid until adop_serve_destroy) and renders requests --
+ * one camera each, any resolution -- into caller-owned device buffers.  The
+ * only device memory it allocates is one block of mem_budget_bytes at
+ * create, from which every admitted request reserves its pixel state
+ * (keys, counts, sums: (12 + 4 c) bytes per pyramid pixel).  A scheduler
+ * thread admits queued requests in FIFO order whenever a slot and memory are
+ * free, groups admitted requests of the same cloud (up to max_batch) into
+ * one launch sequence, and runs batches concurrently on `streams` CUDA
+ * streams; requests that arrive while others run join the next batch.  The
+ * render itself is adop_render_forward's (forward pass of Sec. 3.1 plus the
+ * photometric epilogue of Sec. 3.3 when ADOP_FLAG_EPILOGUE is set and the
+ * camera enables it), so a result is the same alone and in a batch.
+ * Latency = submit to completion of the request's batch on the device.
+ * Not part of the paper: the deployment side of the method.
+ * ---------------------------------------------------------------------- */
+typedef struct adop_server adop_server;
+
+typedef struct {
+    size_t mem_budget_bytes;   /* device memory for pixel state (>= 1 MiB) */
+    int32_t max_slots;         /* requests admitted at once (1..4096) */
+    int32_t streams;           /* batches in flight at once (1..16) */
+    int32_t max_batch;         /* cameras per launch (1..16) */
+    int32_t levels;            /* pyramid layers of every request */
+    float alpha, znear;        /* as in adop_params */
+    uint32_t flags;            /* ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL */
+    adop_dtype out_dtype;      /* output image type */
+    const float* background;   /* c FP32 (device) or NULL */
+} adop_serve_config;
+
+typedef struct {
+    int64_t submitted, completed, cancelled, failed, queued, active, batches;
+    double mean_batch;         /* requests per launched batch */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency since the last reset */
+    double req_per_s, points_per_s;          /* completed since the last reset */
+    size_t mem_in_use, mem_peak;
+} adop_serve_stats;
+
+/* Create a server (allocates the budget and the streams, starts the scheduler). */
+adop_status adop_serve_create(const adop_serve_config* cfg, adop_server** out);
+/* Register a resident cloud; all clouds share c and feat_dtype. */
+adop_status adop_serve_load_cloud(adop_server* s, const adop_points* pts, int32_t* cloud_id);
+/* Queue a render of cloud_id through cam into out_image (device, caller-owned:
+ * all layers concatenated, layer l = c x h_l x w_l planar in out_dtype).
+ * ADOP_ERR_OUT_OF_MEMORY if the request could never fit the budget. */
+adop_status adop_serve_submit(adop_server* s, int32_t cloud_id, const adop_camera* cam, void* out_image,
+                              uint64_t* ticket);
+/* ADOP_OK when done, ADOP_ERR_BUSY while queued or running, or the request's error. */
+adop_status adop_serve_poll(adop_server* s, uint64_t ticket);
+/* Block until the request is done or timeout_ms passes (ADOP_ERR_TIMEOUT). */
+adop_status adop_serve_wait(adop_server* s, uint64_t ticket, int32_t timeout_ms);
+/* Cancel a request still in the queue (ADOP_ERR_BUSY once admitted). */
+adop_status adop_serve_cancel(adop_server* s, uint64_t ticket);
+/* Latency of a finished request in milliseconds. */
+adop_status adop_serve_latency(adop_server* s, uint64_t ticket, double* ms);
+adop_status adop_serve_get_stats(adop_server* s, adop_serve_stats* out);
+adop_status adop_serve_reset_stats(adop_server* s);
+/* Cancel queued requests, finish admitted ones, free everything. */
+adop_status adop_serve_destroy(adop_server* s);
+
 /* Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by a pair of CUDA events recorded on the launch's stream (a few
  * microseconds of host time per launch, no device synchronisation).

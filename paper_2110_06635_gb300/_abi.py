@@ -348,3 +348,117 @@ def adop_render_backward_noalloc(points: Points, cams, params: Params, frames, g
     _check(lib.adop_render_backward_noalloc(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr,
                                             _dev_ptr(grad_feat), _dev_ptr(grad_xyz), _dev_ptr(grad_pose),
                                             _dev_ptr(grad_intr), _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------------------
+# render server (adop_serve_*)
+# ---------------------------------------------------------------------------
+
+class adop_serve_config(ct.Structure):
+    _fields_ = [("mem_budget_bytes", ct.c_size_t), ("max_slots", ct.c_int32), ("streams", ct.c_int32),
+                ("max_batch", ct.c_int32), ("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float),
+                ("flags", ct.c_uint32), ("out_dtype", ct.c_int32), ("background", ct.c_void_p)]
+
+
+class adop_serve_stats(ct.Structure):
+    _fields_ = [(k, ct.c_int64) for k in ("submitted", "completed", "cancelled", "failed", "queued", "active",
+                                          "batches")] + \
+               [(k, ct.c_double) for k in ("mean_batch", "p50_ms", "p99_ms", "mean_ms", "max_ms", "req_per_s",
+                                           "points_per_s")] + \
+               [("mem_in_use", ct.c_size_t), ("mem_peak", ct.c_size_t)]
+
+
+SIGNATURES.update({
+    "adop_serve_create": (ct.c_int, [_P, _P]),
+    "adop_serve_load_cloud": (ct.c_int, [_P, _P, _P]),
+    "adop_serve_submit": (ct.c_int, [_P, ct.c_int32, _P, _P, _P]),
+    "adop_serve_poll": (ct.c_int, [_P, ct.c_uint64]),
+    "adop_serve_wait": (ct.c_int, [_P, ct.c_uint64, ct.c_int32]),
+    "adop_serve_cancel": (ct.c_int, [_P, ct.c_uint64]),
+    "adop_serve_latency": (ct.c_int, [_P, ct.c_uint64, _P]),
+    "adop_serve_get_stats": (ct.c_int, [_P, _P]),
+    "adop_serve_reset_stats": (ct.c_int, [_P]),
+    "adop_serve_destroy": (ct.c_int, [_P]),
+})
+
+
+def output_numel(cam, c: int, levels: int) -> int:
+    """Elements of a server output buffer: all layers, c x h_l x w_l each."""
+    return c * pyramid_offsets(int(cam.w), int(cam.h), levels)[-1]
+
+
+def split_output(buf, cam, c: int, levels: int):
+    """Views of a server output buffer per layer (c x h_l x w_l)."""
+    off = pyramid_offsets(int(cam.w), int(cam.h), levels)
+    return [buf[c * off[l]:c * off[l + 1]].view(c, int(cam.h) >> l, int(cam.w) >> l) for l in range(levels)]
+
+
+class Server:
+    """Continuous-batching render server over adop_serve_* (see include/adop.h)."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 64, streams: int = 4, max_batch: int = 8,
+                 levels: int = 4, alpha: float = 0.01, znear: float = 1e-3, flags: int = 0, out_dtype=None,
+                 background=None):
+        torch = _torch()
+        self.lib = load()
+        self.levels = levels
+        self.out_dtype = out_dtype or torch.float32
+        self._keep = {}
+        self._clouds = []
+        self._bg = background
+        cfg = adop_serve_config(mem_budget_bytes, max_slots, streams, max_batch, levels, alpha, znear, flags,
+                                dtype_code(self.out_dtype), _dev_ptr(background))
+        h = ct.c_void_p()
+        _check(self.lib.adop_serve_create(ct.byref(cfg), ct.byref(h)))
+        self.h = h
+
+    def load_cloud(self, points: Points) -> int:
+        ps = points.struct()
+        cid = ct.c_int32()
+        _check(self.lib.adop_serve_load_cloud(self.h, ct.byref(ps), ct.byref(cid)))
+        self._clouds.append(points)
+        return cid.value
+
+    def submit(self, cloud_id: int, cam, out, crf_lut=None) -> int:
+        cs = camera_struct(cam, crf_lut)
+        t = ct.c_uint64()
+        _check(self.lib.adop_serve_submit(self.h, cloud_id, ct.byref(cs), _dev_ptr(out), ct.byref(t)))
+        self._keep[t.value] = (out, crf_lut)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return int(self.lib.adop_serve_poll(self.h, ticket))
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000) -> int:
+        st = int(self.lib.adop_serve_wait(self.h, ticket, timeout_ms))
+        if st != 6 and st != 5:
+            self._keep.pop(ticket, None)
+        return st
+
+    def cancel(self, ticket: int) -> int:
+        return int(self.lib.adop_serve_cancel(self.h, ticket))
+
+    def latency_ms(self, ticket: int) -> float:
+        v = ct.c_double()
+        _check(self.lib.adop_serve_latency(self.h, ticket, ct.byref(v)))
+        return v.value
+
+    def stats(self) -> dict:
+        s = adop_serve_stats()
+        _check(self.lib.adop_serve_get_stats(self.h, ct.byref(s)))
+        return {k: getattr(s, k) for k, _ in adop_serve_stats._fields_}
+
+    def reset_stats(self):
+        _check(self.lib.adop_serve_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            _check(self.lib.adop_serve_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

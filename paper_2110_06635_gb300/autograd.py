@@ -1,0 +1,134 @@
+"""``torch.autograd.Function`` around the C ABI (Sec. 3.1 forward + backward).
+
+``rasterize(xyz, feat, cameras, xi=None, intrinsics=None, ...)`` renders every
+camera's image pyramid and makes it differentiable with respect to
+
+* ``xyz`` (n x 3) -- through the approximate one-pixel spatial gradient,
+* ``feat`` (n x c, float32 / bfloat16 / float16 storage; its gradient is FP32
+  and is returned in the storage dtype, as autograd requires),
+* ``xi`` (n_cam x 6 tangent-space pose increments, (nu, omega)): the pose
+  used is exp(xi) (R, t) (Eq. tangent).  As in the paper the optimiser
+  updates xi, the caller applies it to the pose and resets it to zero; the
+  gradient is that of the left increment at exp(xi) (R, t), which equals
+  dL/dxi exactly at xi = 0,
+* ``intrinsics`` (n_cam x 6: fx, fy, cx, cy, k1, k2), replacing the cameras'
+  values.
+
+``keep_state=True`` keeps each camera's per-pixel key/count/sum buffers and
+per-point layer mask for the backward pass; ``keep_state=False`` keeps only
+the inputs and the backward pass re-renders the depth and accumulate passes
+(the paper's choice: Lambda is never stored).
+
+All arithmetic runs in the CUDA library; this module only allocates tensors
+and marshals pointers.  The pose exponential (6 numbers per camera) is
+evaluated on the host in FP64.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+import torch
+
+from . import _abi as A
+
+
+def se3_exp(xi) -> np.ndarray:
+    """4x4 SE(3) exponential of xi = (nu, omega) (closed form: Rodrigues for
+    the rotation, the left Jacobian for the translation)."""
+    xi = np.asarray(xi, np.float64)
+    nu, om = xi[:3], xi[3:]
+    th = float(np.linalg.norm(om))
+    K = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
+    if th < 1e-8:
+        R = np.eye(3) + K + 0.5 * K @ K
+        V = np.eye(3) + 0.5 * K + K @ K / 6.0
+    else:
+        a = math.sin(th) / th
+        b = (1 - math.cos(th)) / th ** 2
+        c = (th - math.sin(th)) / th ** 3
+        R = np.eye(3) + a * K + b * K @ K
+        V = np.eye(3) + b * K + c * K @ K
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = V @ nu
+    return T
+
+
+def _effective_cameras(cameras, xi, intrinsics):
+    cams = []
+    xi_h = None if xi is None else xi.detach().to("cpu", torch.float64).numpy()
+    k_h = None if intrinsics is None else intrinsics.detach().to("cpu", torch.float64).numpy()
+    for k, cam in enumerate(cameras):
+        c = copy.copy(cam)
+        if xi_h is not None and np.any(xi_h[k] != 0):
+            T = np.eye(4)
+            T[:3, :3] = np.asarray(cam.R, np.float64)
+            T[:3, 3] = np.asarray(cam.t, np.float64)
+            T = se3_exp(xi_h[k]) @ T
+            c.R = T[:3, :3].astype(np.float32)
+            c.t = T[:3, 3].astype(np.float32)
+        if k_h is not None:
+            c.fx, c.fy, c.cx, c.cy, c.k1, c.k2 = (float(v) for v in k_h[k])
+        cams.append(c)
+    return cams
+
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xyz, feat, xi, intr, cams, params, out_dtype, keep_state, crf_luts):
+        dev = xyz.device
+        levels = params.levels
+        pts = A.Points(xyz.contiguous(), feat.contiguous())
+        frames = [A.Frame.alloc(c, feat.shape[1], levels, out_dtype, keep_state, dev,
+                                xyz.shape[0] if keep_state else None) for c in cams]
+        ws = A.alloc_workspace(pts, cams, params, crf_luts, dev)
+        A.adop_render_forward(pts, cams, params, frames, ws, crf_luts=crf_luts)
+        ctx.save_for_backward(xyz, feat)
+        ctx.frames, ctx.cams, ctx.params, ctx.ws, ctx.crf_luts = frames, cams, params, ws, crf_luts
+        ctx.has_xi, ctx.has_intr = xi is not None, intr is not None
+        ctx.xi_dev = None if xi is None else xi.device
+        ctx.intr_dev = None if intr is None else intr.device
+        return tuple(im for f in frames for im in f.images)
+
+    @staticmethod
+    def backward(ctx, *grad_out):
+        xyz, feat = ctx.saved_tensors
+        dev = xyz.device
+        levels = ctx.params.levels
+        ncam = len(ctx.cams)
+        gimgs = []
+        for k in range(ncam):
+            row = []
+            for l in range(levels):
+                g = grad_out[k * levels + l]
+                row.append(None if g is None else g.to(torch.float32).contiguous())
+            gimgs.append(row)
+        n, c = feat.shape
+        need_xyz = ctx.needs_input_grad[0]
+        need_feat = ctx.needs_input_grad[1]
+        need_pose = ctx.needs_input_grad[2] or ctx.needs_input_grad[3]
+        gfeat = torch.empty((n, c), dtype=torch.float32, device=dev) if need_feat else None
+        gxyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if need_xyz else None
+        gpose = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
+        gintr = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
+        params = A.Params(ctx.params.levels, ctx.params.alpha, ctx.params.znear, ctx.params.background,
+                          ctx.params.flags | A.ADOP_FLAG_GRAD_ASSIGN)
+        pts = A.Points(xyz.contiguous(), feat.contiguous())
+        A.adop_render_backward(pts, ctx.cams, params, ctx.frames, gimgs, gfeat, gxyz, gpose, gintr, ctx.ws,
+                               crf_luts=ctx.crf_luts)
+        g_feat = None if gfeat is None else gfeat.to(feat.dtype)
+        g_xi = None if not ctx.needs_input_grad[2] else gpose.to(ctx.xi_dev)
+        g_intr = None if not ctx.needs_input_grad[3] else gintr.to(ctx.intr_dev)
+        return gxyz, g_feat, g_xi, g_intr, None, None, None, None, None
+
+
+def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01, znear=1e-3, background=None,
+              flags=0, out_dtype=torch.float32, keep_state=True, crf_luts=None):
+    """Differentiable render of every camera; returns [camera][layer] images
+    (c x h_l x w_l).  See the module docstring for the gradients."""
+    cams = _effective_cameras(cameras, xi, intrinsics)
+    params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN)
+    outs = _Rasterize.apply(xyz, feat, xi, intrinsics, cams, params, out_dtype, keep_state, crf_luts)
+    return [list(outs[k * levels:(k + 1) * levels]) for k in range(len(cameras))]

@@ -82,18 +82,6 @@ constexpr int kMaxPartialBlocks = 4096;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-int64_t pyramid_pixels(int32_t w, int32_t h, int levels, int64_t* off) {
-  int64_t o = 0;
-  for (int l = 0; l < levels; ++l) {
-    if (off) off[l] = o;
-    o += (int64_t)(w >> l) * (int64_t)(h >> l);
-  }
-  if (off) {
-    for (int l = levels; l <= ADOP_MAX_LEVELS; ++l) off[l] = o;
-  }
-  return o;
-}
-
 bool finite(float v) { return std::isfinite(v); }
 
 // Workspace: per camera [keys | counts | sums | point layer masks | backward
@@ -227,14 +215,7 @@ adop_status validate_ws(void* ws, size_t ws_bytes, size_t need) {
 // frame if given, else from the workspace.
 void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_frame_state, const WsLayout& L,
               int k, char* ws, const adop_points* pts, const adop_params* prm) {
-  memset(&d, 0, sizeof(d));
-  memcpy(d.R, cam.T.R, sizeof(d.R));
-  memcpy(d.t, cam.T.t, sizeof(d.t));
-  d.fx = cam.K.fx; d.fy = cam.K.fy; d.cx = cam.K.cx; d.cy = cam.K.cy;
-  d.k1 = cam.K.k1; d.k2 = cam.K.k2; d.k3 = cam.K.k3; d.p1 = cam.K.p1; d.p2 = cam.K.p2;
-  d.w = cam.K.w;
-  d.h = cam.K.h;
-  pyramid_pixels(d.w, d.h, prm->levels, d.off);
+  set_camera_constants(d, cam, prm->levels, prm->flags);
   for (int l = 0; l < prm->levels; ++l) {
     if (use_frame_state) {
       d.key[l] = reinterpret_cast<unsigned long long*>(f->key[l]);
@@ -249,14 +230,6 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
   d.vis = use_frame_state ? f->vis : reinterpret_cast<uint8_t*>(ws + L.vis[k]);
   d.info = reinterpret_cast<float*>(ws + L.info[k]);
   d.gpm = reinterpret_cast<float*>(ws + L.gpm[k]);
-  const adop_photometric& ph = cam.ph;
-  d.epi = ((prm->flags & ADOP_FLAG_EPILOGUE) && ph.enabled) ? 1 : 0;
-  d.ev_scale = (float)std::exp2(-(double)ph.ev);
-  for (int j = 0; j < 3; ++j) { d.wb[j] = ph.wb[j]; d.vig_a[j] = ph.vig_a[j]; }
-  d.vig_c[0] = ph.vig_c[0];
-  d.vig_c[1] = ph.vig_c[1];
-  d.crf = ph.crf_lut;
-  d.crf_n = ph.crf_n;
   (void)pts;
 }
 
@@ -321,6 +294,31 @@ std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 }  // namespace
+
+void set_last_error(const char* msg) { g_last_error = msg; }
+
+void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_t flags) {
+  memset(&d, 0, sizeof(d));
+  memcpy(d.R, cam.T.R, sizeof(d.R));
+  memcpy(d.t, cam.T.t, sizeof(d.t));
+  d.fx = cam.K.fx; d.fy = cam.K.fy; d.cx = cam.K.cx; d.cy = cam.K.cy;
+  d.k1 = cam.K.k1; d.k2 = cam.K.k2; d.k3 = cam.K.k3; d.p1 = cam.K.p1; d.p2 = cam.K.p2;
+  d.w = cam.K.w;
+  d.h = cam.K.h;
+  pyramid_pixels(d.w, d.h, levels, d.off);
+  const adop_photometric& ph = cam.ph;
+  d.epi = ((flags & ADOP_FLAG_EPILOGUE) && ph.enabled) ? 1 : 0;
+  d.ev_scale = (float)std::exp2(-(double)ph.ev);
+  for (int j = 0; j < 3; ++j) {
+    d.wb[j] = ph.wb[j];
+    d.vig_a[j] = ph.vig_a[j];
+  }
+  d.vig_c[0] = ph.vig_c[0];
+  d.vig_c[1] = ph.vig_c[1];
+  d.crf = ph.crf_lut;
+  d.crf_n = ph.crf_n;
+}
+
 }  // namespace adop
 
 // File scope, as the entry point's contract states: every device that loads

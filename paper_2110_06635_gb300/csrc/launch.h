@@ -47,6 +47,26 @@ cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const 
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s);
 
+// Pixels of a w x h pyramid of `levels` layers (w_l = w >> l, h_l = h >> l);
+// off (if given) receives the first pixel of every layer and the total.
+inline int64_t pyramid_pixels(int32_t w, int32_t h, int levels, int64_t* off) {
+  int64_t o = 0;
+  for (int l = 0; l < levels; ++l) {
+    if (off) off[l] = o;
+    o += (int64_t)(w >> l) * (int64_t)(h >> l);
+  }
+  if (off)
+    for (int l = levels; l <= ADOP_MAX_LEVELS; ++l) off[l] = o;
+  return o;
+}
+
+// Camera constants of a DevCam (pose, intrinsics, layer offsets, photometric
+// epilogue); buffer pointers are left to the caller.
+void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_t flags);
+
+// Set the calling thread's adop_last_error() message.
+void set_last_error(const char* msg);
+
 // Channel counts with compiled kernels.
 inline bool channels_supported(int c) { return c == 1 || c == 2 || c == 3 || c == 4 || c == 8 || c == 16; }
 
