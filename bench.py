@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="a few steps, no extras (for ncu)")
+    ap.add_argument("--no-train", action="store_true", help="skip the 16-camera training step")
+    ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -372,6 +376,196 @@ def cpu_baseline(budget_s: float = 15.0):
                       f"fwd+bwd, FP64 C oracle, single thread, {t_used:.1f} s"}
 
 
+# ---------------------------------------------------------------------------
+# further workloads, reported beside the headline number
+# ---------------------------------------------------------------------------
+
+def bench_training_step(device, steps: int = 5, warmup: int = 3) -> dict:
+    """20M points, C=8 BF16, 16 orbit cameras 960x540..1920x1080 with their own
+    exposure / white balance / vignette / response curve, forward + backward of
+    all 16 through the autograd.Function, depth pass re-rendered in backward
+    (no per-pixel state kept), FP32 gradient accumulation across cameras."""
+    import torch
+    import paper_2110_06635_gb300 as adop
+    import scenes
+    from paper_2110_06635_gb300.autograd import rasterize
+    sc, cams = scenes.config(3)
+    xyz = torch.from_numpy(sc.xyz).to(device).requires_grad_()
+    feat = torch.from_numpy(sc.feat_as("bf16").view(np.int16)).to(device).view(torch.bfloat16).requires_grad_()
+    luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(device) for c in cams]
+    xi = torch.zeros((len(cams), 6), dtype=torch.float32, device=device, requires_grad=True)
+    G = [[torch.randn(sc.c, c.h >> l, c.w >> l, device=device, generator=torch.Generator(device).manual_seed(k))
+          .to(torch.bfloat16) for l in range(LEVELS)] for k, c in enumerate(cams)]
+    flat_g = [g for row in G for g in row]
+
+    def step():
+        imgs = rasterize(xyz, feat, cams, xi, levels=LEVELS, flags=adop.ADOP_FLAG_EPILOGUE,
+                         out_dtype=torch.bfloat16, keep_state=False, crf_luts=luts)
+        torch.autograd.backward([im for row in imgs for im in row], flat_g)
+
+    for _ in range(warmup):
+        step()
+    adop.adop_profile_enable(True)
+    adop.adop_profile_collect()
+    total_ms, per = timed_steps(step, steps, None, None, device)
+    ks = adop.adop_profile_collect()
+    adop.adop_profile_enable(False)
+    views = len(cams)
+    px = sum(adop.pyramid_offsets(c.w, c.h, LEVELS)[-1] for c in cams)
+    out = {"workload": f"{sc.n} points C=8 BF16, {views} cameras 960x540..1920x1080 ({px} pyramid px), "
+                       "fwd+bwd via autograd, epilogue on, depth re-rendered in backward",
+           "ms_per_step": round(total_ms / steps, 3),
+           "point_views_per_s": round(sc.n * views * steps / (total_ms / 1e3), 1),
+           "gpu_launches_per_step": round(sum(v[0] for v in ks.values()) / steps, 2),
+           "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in ks.items()}}
+    del xyz, feat, G, flat_g
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_large_scene(device, frames: int = 60) -> dict:
+    """120M points (FP32 xyz + 4-channel FP16 descriptors, 2.4 GB) on 500
+    surfaces in a 100 m box; forward only along a 60-frame path at 1920x1080
+    and 3840x2160; 4 layers, alpha = 0.01."""
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+    import scenes
+    from paper_2110_06635_gb300 import _abi as A
+    sc, _ = scenes.config(4)
+    xyz = torch.from_numpy(sc.xyz).to(device)
+    feat = torch.from_numpy(sc.feat.astype(np.float16)).to(device)
+    n = sc.n
+    del sc
+    pts = adop.Points(xyz, feat)
+    params = adop.Params(LEVELS, 0.01, 1e-3, None, 0)
+    res = {}
+    peak, _ = measured_peaks()
+    for (w, h) in ((1920, 1080), (3840, 2160)):
+        cams = scenes.path_cameras(frames, w, h, seed=1004)
+        fr = adop.Frame.alloc(cams[0], 4, LEVELS, torch.float16, False, device)
+        ws = adop.alloc_workspace(pts, [cams[0]], params, None, device)
+        lib = A.load()
+        ps, pr = pts.struct(), params.struct()
+        frs = (A.adop_frame * 1)(fr.struct())
+        wp, wn = A._ws_ptr(ws)
+        sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        carr = [A._cams_array([c]) for c in cams]
+        it = iter(range(10 ** 9))
+
+        def step():
+            k = next(it) % frames
+            st = lib.adop_render_forward(ct.byref(ps), carr[k], 1, ct.byref(pr), frs, wp, wn, sp)
+            if st != 0:
+                raise RuntimeError(lib.adop_last_error().decode())
+
+        for _ in range(3):
+            step()
+        adop.adop_profile_enable(True)
+        adop.adop_profile_collect()
+        total_ms, _ = timed_steps(step, frames, None, None, device)
+        ks = adop.adop_profile_collect()
+        adop.adop_profile_enable(False)
+        px = adop.pyramid_offsets(w, h, LEVELS)[-1]
+        fb = sum(algorithmic_bytes(k, n, px, 4, 2, 2) for k in ks if k in ("clear", "depth", "accumulate", "normalize"))
+        ms = total_ms / frames
+        res[f"{w}x{h}"] = {"fps": round(1e3 / ms, 2), "ms_per_frame": round(ms, 3),
+                           "points_per_s": round(n / (ms / 1e3), 1),
+                           "hbm_fraction_of_measured": round(fb / (ms * 1e-3) / 1e9 / peak, 4),
+                           "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
+        del ws, fr
+        torch.cuda.empty_cache()
+    del xyz, feat, pts
+    torch.cuda.empty_cache()
+    return {"workload": f"{n} points FP32 xyz + C=4 FP16, 60-frame path, forward only, 4 layers", **res}
+
+
+def bench_serving(device, seconds: float = 10.0, rate: float = 200.0) -> dict:
+    """Three resident clouds (1M, 10M, 50M points, C=8); Poisson arrivals at
+    `rate` req/s of random orbit views at 640x480 / 1280x720 / 1920x1080 /
+    3840x2160 (uniform), forward + photometric epilogue.  (i) continuous
+    batching, BF16 descriptors and output; (ii) one request at a time, FP32."""
+    import threading
+    import torch
+    import paper_2110_06635_gb300 as adop
+    import scenes
+    res_set = ((640, 480), (1280, 720), (1920, 1080), (3840, 2160))
+    base = [scenes.surfaces_scene(n, 8, seed=1005 + k, size_scale=scenes.SIZE_SCALE_SINGLE_VIEW)
+            for k, n in enumerate((1_000_000, 10_000_000, 50_000_000))]
+    lut = torch.from_numpy(scenes.crf_gamma_lut()).to(device)
+    out = {}
+    for mode in ("bf16_batched", "fp32_unbatched"):
+        bf16 = mode.startswith("bf16")
+        dt = torch.bfloat16 if bf16 else torch.float32
+        clouds = []
+        for sc in base:
+            f = torch.from_numpy(sc.feat_as("bf16").view(np.int16)).to(device).view(torch.bfloat16) if bf16 \
+                else torch.from_numpy(sc.feat).to(device)
+            clouds.append(adop.Points(torch.from_numpy(sc.xyz).to(device), f))
+        srv = adop.Server(mem_budget_bytes=8 << 30, max_slots=64 if bf16 else 1, streams=4 if bf16 else 1,
+                          max_batch=8 if bf16 else 1, levels=LEVELS, flags=adop.ADOP_FLAG_EPILOGUE, out_dtype=dt)
+        ids = [srv.load_cloud(p) for p in clouds]
+        rng = np.random.default_rng(2026)
+        n_req = int(seconds * rate)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req + int(rate)))
+        reqs = []
+        for k in range(len(arrivals)):
+            w, h = res_set[int(rng.integers(4))]
+            cam = scenes.orbit_cameras(1, seed=int(rng.integers(1 << 30)), resolutions=((w, h),))[0]
+            reqs.append((int(rng.integers(3)), cam))
+        tickets, lock = [], threading.Lock()
+        pending = [0]
+        done_evt = threading.Event()
+
+        def reaper():
+            while not done_evt.is_set() or tickets:
+                with lock:
+                    t = tickets.pop(0) if tickets else None
+                if t is None:
+                    time.sleep(0.0005)
+                    continue
+                srv.wait(t, 120_000)
+                with lock:
+                    pending[0] -= 1
+
+        th = threading.Thread(target=reaper, daemon=True)
+        th.start()
+        warm = int(rate)  # the first second warms up and is not measured
+        t0 = time.perf_counter()
+        for k, ((cid, cam), ta) in enumerate(zip(reqs, arrivals)):
+            if k == warm:
+                # drain the warm-up, then measure from here
+                while True:
+                    with lock:
+                        if pending[0] == 0:
+                            break
+                    time.sleep(0.001)
+                srv.reset_stats()
+                t0 = time.perf_counter() - ta
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            buf = torch.empty(adop.output_numel(cam, 8, LEVELS), dtype=dt, device=device)
+            t = srv.submit(ids[cid], cam, buf, lut)
+            with lock:
+                tickets.append(t)
+                pending[0] += 1
+        done_evt.set()
+        th.join()
+        st = srv.stats()
+        out[mode] = {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                     "mean_ms": round(st["mean_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                     "req_per_s": round(st["req_per_s"], 1), "points_per_s": round(st["points_per_s"], 1),
+                     "completed": st["completed"], "mean_batch": round(st["mean_batch"], 2),
+                     "mem_peak_bytes": st["mem_peak"]}
+        srv.close()
+        del clouds
+        torch.cuda.empty_cache()
+    out["workload"] = (f"clouds of 1M/10M/50M points (C=8), Poisson {rate:.0f} req/s for {seconds:.0f} s after 1 s "
+                       "warm-up, views at 640x480/1280x720/1920x1080/3840x2160, forward + photometric epilogue")
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -422,6 +616,16 @@ def main():
         e2e_ms = max_over_ranks(dist, e2e_ms, device)
         line["e2e"] = {"value": round(world * wl.n * ksteps / (e2e_ms / 1e3), 1), "unit": UNIT,
                        "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    if not args.profile_only:
+        bf = results = wl = None  # free the headline workload before the larger ones
+        import torch
+        torch.cuda.empty_cache()
+        if not args.no_train:
+            line["training_step"] = bench_training_step(device)
+        if not args.no_large:
+            line["large_scene"] = bench_large_scene(device)
+        if not args.no_serve:
+            line["serve"] = bench_serving(device, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -53,6 +53,23 @@ struct LaunchCams {
 // multiple of 4 from c = 3 on so that every pixel starts on 16 bytes.
 __host__ __device__ constexpr int g_stride(int c) { return c <= 2 ? c : (c + 3) / 4 * 4; }
 
+// L2 cache policies (createpolicy, sm_80+): data that other threads will read
+// again soon (per-pixel records) is kept with evict_last; streamed per-point
+// data uses evict_first so that it does not push the records out.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ float4 ld_keep(const float4* ptr, uint64_t pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
+
 // Load n floats (n a multiple of 4, 2, or 1) from a suitably aligned address.
 template <int N>
 __device__ __forceinline__ void load_vec(const float* __restrict__ src, float* dst) {
@@ -71,6 +88,20 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ src, float* d
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) dst[k] = __ldg(src + k);
+  }
+}
+
+// load_vec with the L2 policy on every 16-byte piece (scalar pieces: plain loads).
+template <int N>
+__device__ __forceinline__ void load_keep(const float* __restrict__ src, float* dst, uint64_t pol) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 4; ++v) {
+      const float4 q = ld_keep(reinterpret_cast<const float4*>(src) + v, pol);
+      dst[4 * v] = q.x; dst[4 * v + 1] = q.y; dst[4 * v + 2] = q.z; dst[4 * v + 3] = q.w;
+    }
+  } else {
+    load_vec<N>(src, dst);
   }
 }
 

@@ -186,7 +186,7 @@ __device__ __forceinline__ void block_partials(const BwdArgs& b, float (&red)[12
 template <int C>
 __device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __restrict__ info, int64_t base,
                                              int32_t pu, int32_t pv, int32_t wl, int32_t hl, float z, float a1,
-                                             const float* tau, float& g_u, float& g_v) {
+                                             const float* tau, float& g_u, float& g_v, uint64_t pol) {
   constexpr int GS = g_stride(C);
   float cq[4];
   float4 iq[4];
@@ -196,7 +196,7 @@ __device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __
     const int32_t qu = pu + (s == 0 ? 1 : (s == 1 ? -1 : 0));
     const int32_t qv = pv + (s == 2 ? 1 : (s == 3 ? -1 : 0));
     gq[s] = (qu < 0 || qu >= wl || qv < 0 || qv >= hl) ? -1 : base + (int64_t)qv * wl + qu;
-    iq[s] = gq[s] >= 0 ? __ldg(info + gq[s]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    iq[s] = gq[s] >= 0 ? ld_keep(info + gq[s], pol) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -209,7 +209,7 @@ __device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __
     else wgt = __frcp_rn(1.0f + iq[s].y);                        // joins the fuzzy blend
     if (wgt == 0.0f) continue;
     float G[GS];
-    load_vec<GS>(cam.gpm + gq[s] * GS, G);
+    load_keep<GS>(cam.gpm + gq[s] * GS, G, pol);
     float dot = 0.0f;
 #pragma unroll
     for (int k = 0; k < C; ++k) dot = fmaf(G[k], tau[k], dot);
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
   const float4* info = reinterpret_cast<const float4*>(cam.info);
   const bool spatial_out = b.grad_xyz != nullptr || b.partials != nullptr;
+  const uint64_t pol = policy_evict_last();
   float red[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) red[k] = 0.0f;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
             loaded = true;
           }
           float g_u, g_v;
-          spatial_grad<C>(cam, info, base, pu, pv, wl, hl, X2, a.a1, tau, g_u, g_v);
+          spatial_grad<C>(cam, info, base, pu, pv, wl, hl, X2, a.a1, tau, g_u, g_v, pol);
           const float sc = layer_scale(l);
           du0 = fmaf(g_u, sc, du0);
           dv0 = fmaf(g_v, sc, dv0);
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
   float* pt = s_pt[warp];
   float* acc = s_acc[warp];
   uint8_t* item = s_item[warp];
+  const uint64_t pol = policy_evict_last();
   float red[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) red[k] = 0.0f;
@@ -365,9 +367,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
           const int32_t wl = cam.w >> l, hl = cam.h >> l;
           const int64_t lb = cam.off[l];
           const int64_t gp = lb + (int64_t)pv * wl + pu;
-          const float4 ip = __ldg(info + gp);
+          const float4 ip = ld_keep(info + gp, pol);
           float G[GS];
-          load_vec<GS>(cam.gpm + gp * GS, G);
+          load_keep<GS>(cam.gpm + gp * GS, G, pol);
           float* ap = acc + src * AS;
 #pragma unroll
           for (int c = 0; c < C; ++c) atomicAdd(ap + c, __fdiv_rn(G[c], ip.y));
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
 #pragma unroll
             for (int c = 0; c < C; ++c) tau[c] = sp[3 + c];
             float g_u, g_v;
-            spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, z, a.a1, tau, g_u, g_v);
+            spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, z, a.a1, tau, g_u, g_v, pol);
             const float sc = layer_scale(l);
             atomicAdd(ap + C, g_u * sc);
             atomicAdd(ap + C + 1, g_v * sc);
