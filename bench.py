@@ -206,10 +206,11 @@ def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: 
     return {
         "clear": px * (8 + 4 + 4 * c),                          # write key, count, sums
         "depth": n * 12 + px * 8 * 2,                           # read xyz; read+write keys
-        "accumulate": n * (12 + c * s_feat + 1) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
+        "accumulate": n * (12 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
         "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
-        "bwd_points": n * (1 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # mask, xyz, tau -> dtau, dx
+        "bwd_bin": n * (4 + 4 + 4),                                   # masks (count, scatter) -> list
+        "bwd_points": n * (4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # list, xyz, tau -> dtau, dx
         "bwd_reduce": 0,
     }[kernel]
 

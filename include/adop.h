@@ -129,17 +129,20 @@ typedef struct {
  * (the forward fills them; the backward reads them) or all are NULL (the
  * forward keeps them in the workspace; the backward re-renders them there,
  * as the paper's backward pass does).
- * vis (optional, n bytes, only with key/count/acc): per point, bit l is set
- * iff the point passed the fuzzy depth test at its layer-l pixel, i.e. is in
- * Lambda of that pixel.  The forward writes it; the backward then skips the
- * layers where a point is not in Lambda without looking at any pixel.  It is
- * the result of the same FP32 comparisons, so results do not change. */
+ * vis (optional, n uint32, only with key/count/acc): per point, bit l
+ * (l < 8) is set iff the point passed the fuzzy depth test at its layer-l
+ * pixel, i.e. is in Lambda of that pixel; bits 8..31 hold, for such points,
+ * the 32x32-pixel screen tile of its layer-0 position (row-major over
+ * ceil(w/32) tiles per row, position clamped to the image).  The forward
+ * writes it; the backward then skips the layers where a point is not in
+ * Lambda without looking at any pixel, and visits the points tile by tile.
+ * It is the result of the same FP32 comparisons, so results do not change. */
 typedef struct {
     void* image[ADOP_MAX_LEVELS];
     uint64_t* key[ADOP_MAX_LEVELS];
     uint32_t* count[ADOP_MAX_LEVELS];
     float* acc;
-    uint8_t* vis;
+    uint32_t* vis;
     adop_dtype out_dtype;
 } adop_frame;
 

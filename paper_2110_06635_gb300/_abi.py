@@ -195,7 +195,7 @@ class Frame:
     key: object = None     # int64 (bit pattern of uint64), all layers concatenated
     count: object = None   # int32 (bit pattern of uint32)
     acc: object = None     # float32, pixel-major sums
-    vis: object = None     # uint8 per point: layers where the point is in Lambda
+    vis: object = None     # int32 per point: layer mask (bits 0-7) | screen tile << 8
     w: int = 0
     h: int = 0
     levels: int = 0
@@ -217,7 +217,7 @@ class Frame:
             f.count = torch.empty(px, dtype=torch.int32, device=device)
             f.acc = torch.empty(px * c, dtype=torch.float32, device=device)
             if n_points is not None:
-                f.vis = torch.empty(max(1, n_points), dtype=torch.uint8, device=device)
+                f.vis = torch.empty(max(1, n_points), dtype=torch.int32, device=device)
         return f
 
     def layer(self, buf, l):

@@ -18,6 +18,9 @@ namespace adop {
 
 constexpr int kMaxCamsPerLaunch = 16;
 constexpr int kThreads = 256;
+constexpr int kTileShift = 5;  // 32 x 32 pixel screen tiles for binning the backward's points
+
+__host__ __device__ constexpr int32_t tiles_along(int32_t n) { return (n + (1 << kTileShift) - 1) >> kTileShift; }
 
 // Everything a kernel needs to know about one camera, passed by value in the
 // kernel's parameter space (uniform per block: blockIdx.y selects the camera).
@@ -34,7 +37,12 @@ struct DevCam {
   float* acc;    // pixel-major FP32 sums, c floats per pixel
   float* info;   // backward: per pixel {z_min, |Lambda|, <G, I>, 0}
   float* gpm;    // backward: upstream gradient, pixel-major, g_stride(c) floats per pixel
-  uint8_t* vis;  // per point: bit l set iff the point is in Lambda of its layer-l pixel (or NULL)
+  uint32_t* vis;  // per point: layer mask (bits 0-7) | layer-0 screen tile << 8 (or NULL)
+  // screen-tile binning of the visible points for the backward pass
+  int32_t tiles_x, tiles;    // kTileShift-pixel tiles per row, total
+  int32_t* bin_count;        // per tile: visible points (then the scatter cursor)
+  int32_t* bin_off;          // tiles + 1 exclusive offsets
+  int32_t* bin_list;         // visible point indices, tile by tile (NULL: no binning)
   // photometric epilogue (Sec. 3.3); ev_scale = 2^-EV, computed on the host
   int32_t epi;
   int32_t crf_n;

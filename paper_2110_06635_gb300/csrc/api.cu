@@ -85,11 +85,13 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 bool finite(float v) { return std::isfinite(v); }
 
 // Workspace: per camera [keys | counts | sums | point layer masks | backward
-// pixel info | pixel-major upstream gradient], then the pose/intrinsics block
-// partials.
+// pixel info | pixel-major upstream gradient | tile counts | tile offsets |
+// tile-ordered point list], then the pose/intrinsics block partials.
 struct WsLayout {
   size_t key[ADOP_MAX_CAMERAS], cnt[ADOP_MAX_CAMERAS], acc[ADOP_MAX_CAMERAS], vis[ADOP_MAX_CAMERAS];
   size_t info[ADOP_MAX_CAMERAS], gpm[ADOP_MAX_CAMERAS];
+  size_t bin_count[ADOP_MAX_CAMERAS], bin_off[ADOP_MAX_CAMERAS], bin_list[ADOP_MAX_CAMERAS];
+  bool binning;
   size_t partials;
   size_t total;
 };
@@ -107,12 +109,20 @@ WsLayout layout(const adop_points* pts, const adop_camera* cams, int32_t n_cam, 
     L.acc[k] = o;
     o = align_up(o + (size_t)px * c * 4);
     L.vis[k] = o;
-    o = align_up(o + (size_t)pts->n);
+    o = align_up(o + (size_t)pts->n * 4);
     L.info[k] = o;
     o = align_up(o + (size_t)px * 16);
     L.gpm[k] = o;
     o = align_up(o + (size_t)px * g_stride(c) * 4);
+    const size_t tiles = (size_t)tiles_along(cams[k].K.w) * (size_t)tiles_along(cams[k].K.h);
+    L.bin_count[k] = o;
+    o = align_up(o + tiles * 4);
+    L.bin_off[k] = o;
+    o = align_up(o + (tiles + 1) * 4);
+    L.bin_list[k] = o;
+    o = align_up(o + (size_t)pts->n * 4);
   }
+  L.binning = true;
   L.partials = o;
   o = align_up(o + (size_t)n_cam * kMaxPartialBlocks * 12 * 4);
   L.total = o;
@@ -195,7 +205,7 @@ adop_status validate_frames(const adop_frame* frames, int32_t n_cam, const adop_
       return fail(ADOP_ERR_INVALID_ARG, "camera %d: vis needs key/count/acc", k);
     if (sg == 1)
       for (int l = 0; l < prm->levels; ++l)
-        if (((uintptr_t)f.key[l] & 7) != 0 || ((uintptr_t)f.count[l] & 3) != 0)
+        if (((uintptr_t)f.key[l] & 7) != 0 || ((uintptr_t)f.count[l] & 3) != 0 || ((uintptr_t)f.vis & 3) != 0)
           return fail(ADOP_ERR_INVALID_ARG, "camera %d: misaligned key/count buffer", k);
     if (need_out && f.out_dtype != ADOP_F32 && f.out_dtype != ADOP_BF16 && f.out_dtype != ADOP_F16)
       return fail(ADOP_ERR_INVALID_ARG, "camera %d: unknown output dtype %d", k, (int)f.out_dtype);
@@ -227,9 +237,14 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
     d.image[l] = f ? f->image[l] : nullptr;
   }
   d.acc = use_frame_state ? f->acc : reinterpret_cast<float*>(ws + L.acc[k]);
-  d.vis = use_frame_state ? f->vis : reinterpret_cast<uint8_t*>(ws + L.vis[k]);
+  d.vis = use_frame_state ? f->vis : reinterpret_cast<uint32_t*>(ws + L.vis[k]);
   d.info = reinterpret_cast<float*>(ws + L.info[k]);
   d.gpm = reinterpret_cast<float*>(ws + L.gpm[k]);
+  if (L.binning) {
+    d.bin_count = reinterpret_cast<int32_t*>(ws + L.bin_count[k]);
+    d.bin_off = reinterpret_cast<int32_t*>(ws + L.bin_off[k]);
+    d.bin_list = reinterpret_cast<int32_t*>(ws + L.bin_list[k]);
+  }
   (void)pts;
 }
 
@@ -306,6 +321,8 @@ void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_
   d.w = cam.K.w;
   d.h = cam.K.h;
   pyramid_pixels(d.w, d.h, levels, d.off);
+  d.tiles_x = tiles_along(d.w);
+  d.tiles = d.tiles_x * tiles_along(d.h);
   const adop_photometric& ph = cam.ph;
   d.epi = ((flags & ADOP_FLAG_EPILOGUE) && ph.enabled) ? 1 : 0;
   d.ev_scale = (float)std::exp2(-(double)ph.ev);
@@ -510,6 +527,14 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
     b.partials = want_pose ? reinterpret_cast<float*>(ws + L.partials) : nullptr;
     b.mode = mode;
     b.all_projected = (params->flags & ADOP_FLAG_GRAD_ALL_PROJECTED) ? 1 : 0;
+    bool dense = !b.all_projected;
+    for (int j = 0; j < nc; ++j) dense = dense && lc.c[j].vis != nullptr;
+    if (dense) {
+      if ((e = timed("bwd_bin", s, [&] { return launch_bin(lc, a, b, pts->c, s); })) != cudaSuccess)
+        return cuda_fail(e, "backward binning launch");
+    } else {
+      for (int j = 0; j < nc; ++j) lc.c[j].bin_list = nullptr;
+    }
     if ((e = timed("bwd_points", s, [&] { return launch_bwd_points(lc, a, b, pts->c, pts->feat_dtype, bx, s); })) !=
         cudaSuccess)
       return cuda_fail(e, "backward point pass launch");

@@ -17,7 +17,11 @@
 //                  partial sums.
 //   k_bwd_items    the same when the forward recorded each point's layer
 //                  mask: warps compact their (point, layer) pairs in shared
-//                  memory and process them densely.
+//                  memory and process them densely; with binning, the
+//                  visible points are visited 32x32-pixel screen tile by
+//                  tile, so the pixel records a warp reads stay in cache.
+//   k_bin_*        count the visible points per screen tile, scan, scatter
+//                  their indices tile by tile (and zero the others' gradients).
 //   k_bwd_reduce   sums the block partials in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
     bool touched = false;
     // layers in which the point is in Lambda of its pixel, as recorded by the
     // accumulate pass; without the record every in-bounds layer is examined
-    const uint32_t vmask = cam.vis ? (uint32_t)cam.vis[i] : 0xFFu;
+    const uint32_t vmask = cam.vis ? (cam.vis[i] & 0xFFu) : 0xFFu;
     if (vmask != 0u || b.all_projected) {
       float X0, X1, X2, u0, v0;
       transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
 // lanes are not idle on the (majority of) occluded pairs.  Per-point sums
 // over layers go through shared-memory atomics; the owning lane then applies
 // the chain rule and writes its point's gradients.
-template <int C, typename TF>
+template <int C, typename TF, bool BINNED>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant__ LaunchCams cams,
                                                            const __grid_constant__ PointArgs a,
                                                            const __grid_constant__ BwdArgs b) {
@@ -324,10 +328,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
 #pragma unroll
   for (int k = 0; k < 12; ++k) red[k] = 0.0f;
 
+  // the points to visit: all, in index order, or the visible ones tile by tile
+  const int64_t count = BINNED ? (int64_t)cam.bin_off[cam.tiles] : a.n;
   const int64_t stride = (int64_t)gridDim.x * kWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < a.n; base += stride) {
-    const int64_t i = base + lane;
-    const uint32_t mask = i < a.n ? (uint32_t)__ldcs(cam.vis + i) : 0u;
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < count; base += stride) {
+    const int64_t j = base + lane;
+    const int64_t i = j < count ? (BINNED ? (int64_t)__ldcs(cam.bin_list + j) : j) : a.n;
+    const uint32_t mask = i < a.n ? (__ldcs(cam.vis + i) & 0xFFu) : 0u;
     float X0 = 0.f, X1 = 0.f, X2 = 1.f;
     if (mask) {
       float u0, v0;
@@ -391,6 +398,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       float gf[C];
 #pragma unroll
       for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k];
+      // (binned: the points in no Lambda were already given zero gradients)
       float gx[3] = {0.0f, 0.0f, 0.0f};
       const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];
       if (mask && (du0 != 0.0f || dv0 != 0.0f)) chain_rule(cam, X0, X1, X2, du0, dv0, red, gx);
@@ -399,6 +407,171 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
     __syncwarp();
   }
   if (b.partials != nullptr) block_partials(b, red);
+}
+
+// ---------------------------------------------------------------------------
+// screen-tile binning of the visible points: count, exclusive scan, scatter
+// ---------------------------------------------------------------------------
+
+// Runs of equal keys among consecutive lanes (inactive lanes are runs of
+// their own): the lane's run head, the run length and the lane's rank in it.
+__device__ __forceinline__ void lane_run(uint32_t key, bool active, int lane, int& head, int& len, int& rank) {
+  const uint32_t k = active ? key : (0xFF000000u | (uint32_t)lane);  // tiles < 2^24: never equal to a sentinel
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, k, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || k != prev);
+  head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
+  const int end = above ? __ffs(above) - 1 : 32;
+  len = end - head;
+  rank = lane - head;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ LaunchCams cams,
+                                                        const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
+    const int64_t i = base + lane;
+    const uint32_t v = i < a.n ? __ldg(cam.vis + i) : 0u;
+    const bool active = (v & 0xFFu) != 0u;
+    const uint32_t tile = min(v >> 8, (uint32_t)cam.tiles - 1u);
+    int head, len, rank;
+    lane_run(tile, active, lane, head, len, rank);
+    if (active && rank == 0) atomicAdd(cam.bin_count + tile, len);
+  }
+}
+
+// One block per camera: exclusive scan of the tile counts; the counts become
+// the scatter cursors (= the offsets).
+__global__ void __launch_bounds__(1024) k_bin_scan(const __grid_constant__ LaunchCams cams) {
+  const DevCam& cam = cams.c[blockIdx.x];
+  __shared__ int32_t warp_sum[32];
+  const int T = cam.tiles;
+  const int per = (T + 1023) / 1024;
+  const int t0 = threadIdx.x * per;
+  int32_t local = 0;
+  for (int t = t0; t < min(t0 + per, T); ++t) local += cam.bin_count[t];
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = warp_sum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sum[lane] = w;
+  }
+  __syncthreads();
+  int32_t run = incl - local + (warp > 0 ? warp_sum[warp - 1] : 0);
+  for (int t = t0; t < min(t0 + per, T); ++t) {
+    const int32_t c = cam.bin_count[t];
+    cam.bin_off[t] = run;
+    cam.bin_count[t] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) cam.bin_off[T] = warp_sum[31];
+}
+
+template <int C>
+__global__ void __launch_bounds__(kThreads) k_bin_scatter(const __grid_constant__ LaunchCams cams,
+                                                          const __grid_constant__ PointArgs a,
+                                                          const __grid_constant__ BwdArgs b) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
+    const int64_t i = base + lane;
+    const uint32_t v = i < a.n ? __ldg(cam.vis + i) : 0u;
+    const bool active = (v & 0xFFu) != 0u;
+    const uint32_t tile = min(v >> 8, (uint32_t)cam.tiles - 1u);
+    int head, len, rank;
+    lane_run(tile, active, lane, head, len, rank);
+    int32_t slot = 0;
+    if (active && rank == 0) slot = atomicAdd(cam.bin_count + tile, len);
+    slot = __shfl_sync(0xffffffffu, slot, head) + rank;
+    if (active) {
+      cam.bin_list[slot] = (int32_t)i;
+    } else if (i < a.n && b.mode == kGradAssign) {
+      const float zf[C] = {};
+      const float zx[3] = {0.0f, 0.0f, 0.0f};
+      write_point_grads<C>(b, i, zf, zx, false);
+    }
+  }
+}
+
+// Block-local binning (tiles <= kBinSmemTiles): every block takes one
+// contiguous chunk of points, so it touches few tiles; it counts them in
+// shared memory and issues one global atomic per touched tile, instead of
+// one per run of lanes (which serialises on the few tiles that a surface
+// being streamed covers).
+constexpr int kBinSmemTiles = 8192;
+constexpr int kBinBlocksPerSm = 4;
+
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t& c0, int64_t& c1) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  c0 = (int64_t)blockIdx.x * per;
+  c1 = min(n, c0 + per);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_count_blk(const __grid_constant__ LaunchCams cams,
+                                                            const __grid_constant__ PointArgs a) {
+  extern __shared__ int32_t bins[];
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int T = cam.tiles;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) bins[t] = 0;
+  __syncthreads();
+  int64_t c0, c1;
+  chunk_of(a.n, c0, c1);
+#pragma unroll 4
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const uint32_t v = __ldg(cam.vis + i);
+    if (v & 0xFFu) atomicAdd(bins + min(v >> 8, (uint32_t)T - 1u), 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x)
+    if (bins[t]) atomicAdd(cam.bin_count + t, bins[t]);
+}
+
+template <int C>
+__global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_constant__ LaunchCams cams,
+                                                              const __grid_constant__ PointArgs a,
+                                                              const __grid_constant__ BwdArgs b) {
+  extern __shared__ int32_t bins[];  // counts, then this block's next slot per tile
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int T = cam.tiles;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) bins[t] = 0;
+  __syncthreads();
+  int64_t c0, c1;
+  chunk_of(a.n, c0, c1);
+#pragma unroll 4
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const uint32_t v = __ldg(cam.vis + i);
+    if (v & 0xFFu) atomicAdd(bins + min(v >> 8, (uint32_t)T - 1u), 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x)
+    if (bins[t]) bins[t] = atomicAdd(cam.bin_count + t, bins[t]);
+  __syncthreads();
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const uint32_t v = __ldg(cam.vis + i);
+    if (v & 0xFFu) {
+      cam.bin_list[atomicAdd(bins + min(v >> 8, (uint32_t)T - 1u), 1)] = (int32_t)i;
+    } else if (b.mode == kGradAssign) {
+      const float zf[C] = {};
+      const float zx[3] = {0.0f, 0.0f, 0.0f};
+      write_point_grads<C>(b, i, zf, zx, false);
+    }
+  }
 }
 
 // One block per camera, warp k sums element k over all block partials.
@@ -428,12 +601,42 @@ cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const 
                               adop_dtype fd, int blocks_x, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   const dim3 grid(blocks_x, a.ncam);
-  bool dense = !b.all_projected;
-  for (int k = 0; k < a.ncam; ++k) dense = dense && cams.c[k].vis != nullptr;
-  if (dense) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  bool dense = !b.all_projected, binned = true;
+  for (int k = 0; k < a.ncam; ++k) {
+    dense = dense && cams.c[k].vis != nullptr;
+    binned = binned && cams.c[k].bin_list != nullptr;
+  }
+  if (dense && binned) {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF, true><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  } else if (dense) {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF, false><<<grid, kThreads, 0, s>>>(cams, a, b)));
   } else {
     ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_points<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  for (int k = 0; k < a.ncam; ++k) {
+    cudaError_t e = cudaMemsetAsync(cams.c[k].bin_count, 0, sizeof(int32_t) * (size_t)cams.c[k].tiles, s);
+    if (e != cudaSuccess) return e;
+  }
+  int most = 0;
+  for (int k = 0; k < a.ncam; ++k) most = cams.c[k].tiles > most ? cams.c[k].tiles : most;
+  if (most <= kBinSmemTiles) {
+    const size_t smem = sizeof(int32_t) * (size_t)most;
+    int64_t want = (int64_t)num_sms() * kBinBlocksPerSm;
+    want = (want + a.ncam - 1) / a.ncam;
+    const dim3 grid((unsigned)(want < 1 ? 1 : want), a.ncam);
+    k_bin_count_blk<<<grid, kThreads, smem, s>>>(cams, a);
+    k_bin_scan<<<a.ncam, 1024, 0, s>>>(cams);
+    ADOP_DISPATCH_C(c, k_bin_scatter_blk<kC><<<grid, kThreads, smem, s>>>(cams, a, b));
+  } else {
+    const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
+    k_bin_count<<<grid, kThreads, 0, s>>>(cams, a);
+    k_bin_scan<<<a.ncam, 1024, 0, s>>>(cams);
+    ADOP_DISPATCH_C(c, k_bin_scatter<kC><<<grid, kThreads, 0, s>>>(cams, a, b));
   }
   return cudaGetLastError();
 }

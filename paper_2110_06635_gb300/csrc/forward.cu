@@ -57,8 +57,9 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
 // K1 depth pass: key[l][p] = min over points of (bits(z) << 32 | i)
 // One thread per point; the key is read first and the 64-bit atomicMin is
 // issued only if the point can still win (most points are occluded).
-// (Grouping lanes that share a pixel with __match_any_sync before the atomic
-// was measured 4x slower on GB300: the per-group warp intrinsics serialise.)
+// (Measured on GB300: grouping lanes that share a pixel with
+// __match_any_sync was 4x slower -- the per-group warp intrinsics serialise
+// -- and reading all layers' keys before the atomics was 15% slower.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
@@ -83,9 +84,10 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
 // K2 accumulate: points with z <= f32(z_min * (1 + alpha)) add their
 // descriptor to the pixel's FP32 sum (float4 vector atomics) and increment
 // |Lambda|; each point's layer mask of passed tests is written for the
-// backward pass.
+// backward pass, with the point's layer-0 screen tile in bits 8..31.  As in
+// K1, every layer's key is read before the tests.
 // ---------------------------------------------------------------------------
-template <int C, typename TF>
+template <int C, typename TF, int kL>
 __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
   const DevCam& cam = cams.c[blockIdx.y];
@@ -96,24 +98,39 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
     if ((X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
       camera(cam, X0, X1, X2, u0, v0);
+      int64_t pix[kL];
+      uint32_t zb[kL];
+#pragma unroll
+      for (int l = 0; l < kL; ++l) {
+        int32_t pu, pv;
+        pix[l] = (l < a.levels && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? (int64_t)pv * (cam.w >> l) + pu : -1;
+      }
+#pragma unroll
+      for (int l = 0; l < kL; ++l)
+        zb[l] = pix[l] >= 0 ? (uint32_t)(__ldg(cam.key[l] + pix[l]) >> 32) : 0u;
       float f[C];
       bool loaded = false;
-      for (int l = 0; l < a.levels; ++l) {
-        int32_t pu, pv;
-        if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
-        const int64_t p = (int64_t)pv * (cam.w >> l) + pu;
-        const float minz = __uint_as_float((uint32_t)(__ldg(cam.key[l] + p) >> 32));
-        if (!(X2 <= __fmul_rn(minz, a.a1))) continue;
+#pragma unroll
+      for (int l = 0; l < kL; ++l) {
+        if (pix[l] < 0 || !(X2 <= __fmul_rn(__uint_as_float(zb[l]), a.a1))) continue;
         if (!loaded) {
           load_feat<C, TF>(feat, i, f);
           loaded = true;
         }
-        atomic_add_vec<C>(cam.acc + (cam.off[l] + p) * C, f);
-        atomicAdd(cam.cnt[l] + p, 1u);
+        atomic_add_vec<C>(cam.acc + (cam.off[l] + pix[l]) * C, f);
+        atomicAdd(cam.cnt[l] + pix[l], 1u);
         mask |= 1u << l;
       }
     }
-    if (cam.vis) cam.vis[i] = (uint8_t)mask;
+    if (cam.vis) {
+      uint32_t tile = 0;
+      if (mask) {  // layer-0 screen tile of the point (position clamped to the image)
+        const int32_t tu = min(max(__float2int_rn(u0), 0), cam.w - 1) >> kTileShift;
+        const int32_t tv = min(max(__float2int_rn(v0), 0), cam.h - 1) >> kTileShift;
+        tile = (uint32_t)(tv * cam.tiles_x + tu);
+      }
+      cam.vis[i] = (tile << 8) | mask;
+    }
   }
 }
 
@@ -188,7 +205,11 @@ cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_
 cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF><<<grid, kThreads, 0, s>>>(cams, a)));
+  if (a.levels <= 4) {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF, 4><<<grid, kThreads, 0, s>>>(cams, a)));
+  } else {
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF, ADOP_MAX_LEVELS><<<grid, kThreads, 0, s>>>(cams, a)));
+  }
   return cudaGetLastError();
 }
 

@@ -54,6 +54,6 @@ def test_algorithmic_bytes_model():
     import bench
     n, px, c = 1000, 500, 8
     assert bench.algorithmic_bytes("depth", n, px, c, 2, 2) == n * 12 + px * 16
-    assert bench.algorithmic_bytes("bwd_points", n, px, c, 2, 2) == n * (1 + 12 + 16 + 32 + 12) + px * 48
+    assert bench.algorithmic_bytes("bwd_points", n, px, c, 2, 2) == n * (4 + 12 + 16 + 32 + 12) + px * 48
     with pytest.raises(KeyError):
         bench.algorithmic_bytes("nope", n, px, c, 2, 2)
