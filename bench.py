@@ -186,6 +186,25 @@ def gpu_index(device) -> str:
     return u if u.startswith("GPU-") else f"GPU-{u}"
 
 
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/ncu_traffic.json), or None if the kernel's sources changed
+    since the capture (source hash mismatch) or none was recorded."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    h = hashlib.sha1()
+    for rel in d["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return d["dram_bytes_per_launch"] if h.hexdigest() == d["sources_sha1"] else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -199,18 +218,20 @@ def measured_peaks():
 # the workload
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: int) -> int:
+def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: int, n_vis: int | None = None) -> int:
     """Compulsory HBM bytes of one launch: every input read once, every output
-    written once (per camera; n points, px pyramid pixels, c channels)."""
+    written once (per camera; n points, px pyramid pixels, c channels, n_vis
+    points in Lambda of at least one layer)."""
     gs = c if c <= 2 else (c + 3) // 4 * 4
+    nv = n if n_vis is None else n_vis
     return {
         "clear": px * (8 + 4 + 4 * c),                          # write key, count, sums
         "depth": n * 12 + px * 8 * 2,                           # read xyz; read+write keys
         "accumulate": n * (12 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
         "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
-        "bwd_bin": n * (4 + 4 + 4),                                   # masks (count, scatter) -> list
-        "bwd_points": n * (4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # list, xyz, tau -> dtau, dx
+        "bwd_bin": n * 8 + nv * 4 + (n - nv) * (4 * c + 12),          # masks twice -> list; zero grads
+        "bwd_points": nv * (4 + 4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # list, mask, xyz, tau -> grads
         "bwd_reduce": 0,
     }[kernel]
 
@@ -303,6 +324,7 @@ def run_ours(args, dist, rank, world):
         for _ in range(args.warmup):
             wl.step(sp)
         torch.cuda.synchronize()
+        wl.n_vis = int(((wl.frame.vis & 0xFF) != 0).sum().item())
         adop.adop_profile_enable(True)
         adop.adop_profile_collect()
         sampler = ClockSampler(gpu_index(device))
@@ -583,14 +605,14 @@ def main():
     ks = bf["kstats"]
     dom = max(ks, key=lambda k: ks[k][1])
     launches, dom_ms = ks[dom]
-    ab = algorithmic_bytes(dom, wl.n, wl.px, wl.c, wl.s_feat, 2)
+    ab = algorithmic_bytes(dom, wl.n, wl.px, wl.c, wl.s_feat, 2, wl.n_vis)
     achieved = ab / (dom_ms / launches * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback", "traffic": None,
+                if peak_kind == "measured" else "fallback", "traffic": recorded_traffic(dom),
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": round(dom_ms / launches, 4)}
     kernel_ms = {k: round(v[1] / v[0], 4) for k, v in ks.items()}
-    step_bytes = sum(algorithmic_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, 2) for k in ks)
+    step_bytes = sum(algorithmic_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, 2, wl.n_vis) for k in ks)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -599,6 +621,7 @@ def main():
                                "C=8 BF16 descriptors, 4 layers, alpha=0.01, fwd+bwd to tau, x, pose, intrinsics",
                    "points": wl.n, "resolution": "1920x1080", "channels": wl.c, "levels": LEVELS,
                    "feat_dtype": "bf16", "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "points_in_lambda": wl.n_vis,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "kernel_ms": kernel_ms,
