@@ -61,7 +61,8 @@ def _load():
         lib.orc_pyramid_pixels.argtypes = [ct.c_int32, ct.c_int32, ct.c_int]
         lib.orc_pyramid_pixels.restype = ct.c_int64
         lib.orc_forward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P, ct.c_int32, ct.c_float,
-                                    ct.c_float, _P, _P, _P, _P, _P, _P]
+                                    ct.c_float, _P, _P, _P, ct.c_float, _P, _P, _P, _P, _P]
+        lib.orc_knn_radius.argtypes = [ct.c_int64, _P, ct.c_int32, _P]
         lib.orc_forward.restype = ct.c_int
         lib.orc_project_jac_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.orc_camera_f64.argtypes = [_P, _P, _P]
@@ -188,8 +189,19 @@ def feat_to_f64(feat) -> np.ndarray:
     return f.astype(np.float64)
 
 
-def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None) -> Forward:
-    """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend)."""
+def knn_radius(xyz, k: int = 4) -> np.ndarray:
+    """Distance to the k-th nearest other point (FP64, exhaustive; small clouds)."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    out = np.empty(xyz.shape[0])
+    lib.orc_knn_radius(xyz.shape[0], _ptr(xyz), int(k), _ptr(out))
+    return out
+
+
+def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None,
+            radius=None, beta=None, gamma=1.5) -> Forward:
+    """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend);
+    with radius/beta, stochastic point discarding (Eq. discard) at every layer."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
     f64 = np.ascontiguousarray(feat_to_f64(feat))
@@ -203,10 +215,12 @@ def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, n
     z = np.empty(n, dtype=np.float32)
     bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
     nrm = None if normals is None else np.ascontiguousarray(normals, dtype=np.float32)
+    rad = None if radius is None else np.ascontiguousarray(radius, dtype=np.float32)
+    bet = None if radius is None else np.ascontiguousarray(beta, dtype=np.float32)
     K, T = _intr(cam), _pose(cam)
     rc = lib.orc_forward(n, _ptr(xyz), c, _ptr(f64), _ptr(nrm), ct.byref(K), ct.byref(T), int(levels),
-                         ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(keys), _ptr(cnt), _ptr(img),
-                         _ptr(pix), _ptr(z))
+                         ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(rad), _ptr(bet), ct.c_float(gamma),
+                         _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
     if rc != 0:
         raise MemoryError("oracle forward: allocation failed")
     return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)

@@ -148,8 +148,23 @@ int64_t orc_pyramid_pixels(int32_t w, int32_t h, int levels) {
  * boundscheck).  The normal test is taken literally from the paper:
  * keep iff (R n)^T (R x + t) / |R x + t| > 0; the positive norm does not
  * change the sign, so it is evaluated as an FP32 dot product. */
+/* Eq. discard (stochastic point discarding): render the point at layer l
+ * only if r_screen / sqrt(1 - beta) > 1 / gamma, with the world radius
+ * projected as r_screen = fx r_world / (z 2^l) (a pinhole reading: the paper
+ * does not spell the projection out).  Both sides are positive, so the test
+ * is evaluated without the square root as (gamma r_screen)^2 > 1 - beta, in
+ * this FP32 order: t = (f32(fx 2^-l) * r) / z; keep iff (t * t) * f32(gamma *
+ * gamma) > 1 - beta. */
+static int discard_keep(const orc_intrinsics* K, float z, float r, float beta, float gamma, int l) {
+    float fxl = K->fx * ldexpf(1.0f, -l);
+    float t = (fxl * r) / z;
+    float g2 = gamma * gamma;
+    return (t * t) * g2 > 1.0f - beta;
+}
+
 static void project_all(int64_t n, const float* xyz, const float* normals,
                         const orc_intrinsics* K, const orc_pose* T, int levels, float znear,
+                        const float* radius, const float* beta, float gamma,
                         int32_t* pix, float* zf) {
     for (int64_t i = 0; i < n; ++i) {
         float X[3], u0, v0;
@@ -174,7 +189,8 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
         }
         for (int l = 0; l < levels; ++l) {
             int32_t pu, pv;
-            if (keep && orc_pixel(u0, v0, l, K->w, K->h, &pu, &pv))
+            int keep_l = keep && (!radius || discard_keep(K, z, radius[i], beta[i], gamma, l));
+            if (keep_l && orc_pixel(u0, v0, l, K->w, K->h, &pu, &pv))
                 pix[i * levels + l] = pv * (K->w >> l) + pu;
             else
                 pix[i * levels + l] = -1;
@@ -191,6 +207,8 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
  *   feat       n x c, double
  *   background c doubles or NULL (= 0): the value of an empty pixel.  The
  *              paper samples an environment map there; a constant stands in.
+ *   radius, beta, gamma  stochastic discarding (Eq. discard): per-point world
+ *              radius and uniform draw in [0,1); radius NULL = no discarding.
  * Outputs (all over the concatenated pyramid of `levels` layers):
  *   keys  uint64 per pixel; cnt  |Lambda| per pixel; img  c x h_l x w_l;
  *   pix   n x levels pixel id or -1 (may be NULL); zf  n depths (may be NULL).
@@ -199,6 +217,7 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
 int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, const float* normals,
                 const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
                 float znear, const double* background,
+                const float* radius, const float* beta, float gamma,
                 uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out) {
     int64_t npx = orc_pyramid_pixels(K->w, K->h, levels);
     int32_t* pix = pix_out ? pix_out : (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * levels + 1));
@@ -208,7 +227,7 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
 
     /* Step 1: project every point to every layer (Eqs. projection, round,
      * boundscheck, normalculling). */
-    project_all(n, xyz, normals, K, T, levels, znear, pix, zf);
+    project_all(n, xyz, normals, K, T, levels, znear, radius, beta, gamma, pix, zf);
 
     /* Step 2: nearest depth per pixel, as a (depth bits, index) key so that
      * equal depths resolve to the smallest point index. */
@@ -532,4 +551,35 @@ void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const
     if (grad)
         for (int ch = cc; ch < c; ++ch)
             for (int64_t p = 0; p < np; ++p) grad[(int64_t)ch * np + p] = 1.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* World radius for stochastic discarding (Sec. 3.1)                   */
+/* ------------------------------------------------------------------ */
+
+/* r_world[i] = distance from point i to its k-th nearest other point (the
+ * paper uses k = 4), by exhaustive search in FP64; +inf if fewer than k
+ * other points exist.  O(n^2): for test-sized clouds. */
+void orc_knn_radius(int64_t n, const float* xyz, int32_t k, double* radius) {
+    double best[64];
+    for (int64_t i = 0; i < n; ++i) {
+        int m = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = (double)xyz[3 * j] - xyz[3 * i];
+            double dy = (double)xyz[3 * j + 1] - xyz[3 * i + 1];
+            double dz = (double)xyz[3 * j + 2] - xyz[3 * i + 2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            if (m < k) {
+                int q = m++;
+                while (q > 0 && best[q - 1] > d2) { best[q] = best[q - 1]; --q; }
+                best[q] = d2;
+            } else if (d2 < best[k - 1]) {
+                int q = k - 1;
+                while (q > 0 && best[q - 1] > d2) { best[q] = best[q - 1]; --q; }
+                best[q] = d2;
+            }
+        }
+        radius[i] = m < k ? INFINITY : sqrt(best[k - 1]);
+    }
 }
