@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="a few steps, no extras (for ncu)")
     ap.add_argument("--no-train", action="store_true", help="skip the 16-camera training step")
+    ap.add_argument("--no-discard", action="store_true", help="skip the stochastic-discarding variant")
     ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -237,7 +238,7 @@ def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: 
 
 
 class Workload:
-    def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None):
+    def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None, discard: bool = False):
         import torch
         import paper_2110_06635_gb300 as adop
         import scenes
@@ -256,8 +257,20 @@ class Workload:
         else:
             self.feat = torch.from_numpy(scene.feat).to(device)
         self.out_dtype = tdt
-        self.pts = adop.Points(self.xyz, self.feat)
-        self.params = adop.Params(LEVELS, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+        self.radius = self.beta = None
+        flags = adop.ADOP_FLAG_GRAD_ASSIGN
+        if discard:
+            # the paper's preprocess (4th-nearest-point radius) and a fixed uniform draw per point
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.radius = adop.adop_point_radius(self.xyz, 4)
+            torch.cuda.synchronize()
+            self.radius_ms = (time.perf_counter() - t0) * 1e3
+            g = torch.Generator(device=device).manual_seed(1234)
+            self.beta = torch.rand(scene.n, generator=g, device=device)
+            flags |= adop.ADOP_FLAG_DISCARD
+        self.pts = adop.Points(self.xyz, self.feat, None, self.radius, self.beta)
+        self.params = adop.Params(LEVELS, 0.01, 1e-3, None, flags, 1.5)
         self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device, self.n)
         self.ws = adop.alloc_workspace(self.pts, [cam], self.params, None, device)
         G = scenes.upstream_grad(cam.w, cam.h, LEVELS, self.c, 2024)
@@ -340,6 +353,36 @@ def run_ours(args, dist, rank, world):
             del wl
             torch.cuda.empty_cache()
     return results, clocks, device
+
+
+def bench_discard(device, steps: int, warmup: int, flush) -> dict:
+    """The headline workload with stochastic point discarding (Eq. discard,
+    gamma = 1.5, the paper's timed configuration): r_world from the 4th
+    nearest point (GPU preprocess, timed separately), beta ~ U[0,1) fixed."""
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+    wl = Workload(5_000_000, "bf16", device, discard=True)
+    sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(warmup):
+        wl.step(sp)
+    torch.cuda.synchronize()
+    m = wl.frame.vis & 0xFF
+    kept = [float(((m >> l) & 1).sum().item()) for l in range(LEVELS)]
+    adop.adop_profile_enable(True)
+    adop.adop_profile_collect()
+    total_ms, _ = timed_steps(lambda: wl.step(sp), steps, flush, None, device)
+    ks = adop.adop_profile_collect()
+    adop.adop_profile_enable(False)
+    out = {"workload": "the headline view with stochastic discarding, gamma = 1.5",
+           "value": round(wl.n * steps / (total_ms / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(total_ms / steps, 4),
+           "points_in_lambda_per_layer": kept,
+           "radius_preprocess_ms": round(wl.radius_ms, 2),
+           "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 def e2e_measure(wl, steps: int, warmup: int, device):
@@ -644,6 +687,10 @@ def main():
         bf = results = wl = None  # free the headline workload before the larger ones
         import torch
         torch.cuda.empty_cache()
+        if not args.no_discard:
+            fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+            line["stochastic_discard"] = bench_discard(device, args.steps, args.warmup, lambda: fb.zero_())
+            del fb
         if not args.no_train:
             line["training_step"] = bench_training_step(device)
         if not args.no_large:

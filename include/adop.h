@@ -93,7 +93,10 @@ typedef struct {
 /* The point cloud: positions x (n x 3 FP32, 16-byte aligned), neural
  * descriptors tau (n x c, feat_dtype, 16-byte aligned), optional normals
  * (n x 3 FP32, used only with ADOP_FLAG_NORMAL_CULL).  c in {1,2,3,4,8,16};
- * n < 2^31. */
+ * n < 2^31.  radius and beta (n FP32 each, used only with
+ * ADOP_FLAG_DISCARD): the world radius r_world of each point (e.g. from
+ * adop_point_radius) and its uniform draw beta in [0, 1) for stochastic
+ * point discarding (Sec. 3.1, Eq. discard). */
 typedef struct {
     int64_t n;
     int32_t c;
@@ -101,23 +104,33 @@ typedef struct {
     const float* xyz;
     const void* feat;
     const float* normals;
+    const float* radius;
+    const float* beta;
 } adop_points;
 
 #define ADOP_FLAG_NORMAL_CULL (1u << 0)       /* Eq. normalculling; needs normals */
 #define ADOP_FLAG_GRAD_ALL_PROJECTED (1u << 1)/* spatial gradients also for occluded points */
 #define ADOP_FLAG_EPILOGUE (1u << 2)          /* apply the photometric model (fwd and bwd) */
 #define ADOP_FLAG_GRAD_ASSIGN (1u << 3)       /* grad_feat / grad_xyz are overwritten, not += */
+#define ADOP_FLAG_DISCARD (1u << 4)           /* stochastic point discarding, Eq. discard */
 
 /* levels: pyramid layers L (1..ADOP_MAX_LEVELS); alpha: fuzzy depth-test
  * threshold of Eq. depthtest (the paper uses 0.01); znear: points with
  * depth z <= znear are discarded; background: c FP32 values (device) shown
- * where no point lands (the paper's environment map), NULL = zeros. */
+ * where no point lands (the paper's environment map), NULL = zeros.
+ * gamma (> 0, the paper uses 1.5): with ADOP_FLAG_DISCARD a point is
+ * rendered at layer l only if r_screen / sqrt(1 - beta) > 1 / gamma, where
+ * r_screen = fx r_world / (z 2^l); evaluated in FP32 as
+ * (t * t) * f32(gamma * gamma) > 1 - beta with t = (f32(fx 2^-l) * r_world) / z.
+ * A discarded (point, layer) pair takes no part in the depth test, the blend
+ * or the gradients of that layer. */
 typedef struct {
     int32_t levels;
     float alpha;
     float znear;
     const float* background;
     uint32_t flags;
+    float gamma;
 } adop_params;
 
 /* Per-camera frame.  image[l]: output, c x h_l x w_l planar in out_dtype
@@ -302,6 +315,22 @@ typedef struct {
 
 adop_status adop_profile_enable(int32_t on);
 int32_t adop_profile_collect(adop_kernel_stat* out, int32_t max);
+
+/*
+ * World radius of every point for stochastic discarding (Sec. 3.1): the
+ * distance to its k-th nearest other point (the paper uses k = 4), by a
+ * uniform-grid search on the GPU with cells of 1.5x the median k-NN distance
+ * of 256 sampled points; +inf if the cloud has fewer than k + 1 points.
+ * Exact (FP32 distances) when the k-th neighbour lies within 8 cells and at
+ * most 65536 candidates are scanned for the point; otherwise an upper bound
+ * (isolated outliers, which discarding keeps anyway).  xyz: n x 3 FP32
+ * (device); radius: n FP32 (device, output); 1 <= k <= 16.  A preprocess: it
+ * synchronises `stream` once (to size the grid).  Workspace from
+ * adop_point_radius_workspace_bytes(n).
+ */
+size_t adop_point_radius_workspace_bytes(int64_t n);
+adop_status adop_point_radius(const float* xyz, int64_t n, int32_t k, float* radius, void* workspace,
+                              size_t workspace_bytes, adop_stream stream);
 
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* adop_last_error(void);

@@ -20,6 +20,7 @@ ADOP_FLAG_NORMAL_CULL = 1 << 0
 ADOP_FLAG_GRAD_ALL_PROJECTED = 1 << 1
 ADOP_FLAG_EPILOGUE = 1 << 2
 ADOP_FLAG_GRAD_ASSIGN = 1 << 3
+ADOP_FLAG_DISCARD = 1 << 4
 ADOP_F32, ADOP_BF16, ADOP_F16 = 0, 1, 2
 
 STATUS = {0: "ADOP_OK", 1: "ADOP_ERR_INVALID_ARG", 2: "ADOP_ERR_UNSUPPORTED", 3: "ADOP_ERR_OUT_OF_MEMORY",
@@ -52,12 +53,12 @@ class adop_camera(ct.Structure):
 
 class adop_points(ct.Structure):
     _fields_ = [("n", ct.c_int64), ("c", ct.c_int32), ("feat_dtype", ct.c_int32), ("xyz", ct.c_void_p),
-                ("feat", ct.c_void_p), ("normals", ct.c_void_p)]
+                ("feat", ct.c_void_p), ("normals", ct.c_void_p), ("radius", ct.c_void_p), ("beta", ct.c_void_p)]
 
 
 class adop_params(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float), ("background", ct.c_void_p),
-                ("flags", ct.c_uint32)]
+                ("flags", ct.c_uint32), ("gamma", ct.c_float)]
 
 
 class adop_frame(ct.Structure):
@@ -81,6 +82,8 @@ SIGNATURES = {
     "adop_last_error": (ct.c_char_p, []),
     "adop_abi_version": (ct.c_int32, []),
     "adop_render_backward_noalloc": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "adop_point_radius_workspace_bytes": (ct.c_size_t, [ct.c_int64]),
+    "adop_point_radius": (ct.c_int, [_P, ct.c_int64, ct.c_int32, _P, _P, ct.c_size_t, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
     "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
 }
@@ -139,16 +142,20 @@ def dtype_code(dt) -> int:
 
 @dataclass
 class Points:
-    """The point cloud: xyz (n x 3 float32), feat (n x c float32/bfloat16/float16), optional normals."""
+    """The point cloud: xyz (n x 3 float32), feat (n x c float32/bfloat16/float16),
+    optional normals, and for stochastic discarding a world radius and a
+    uniform draw per point (float32, n each)."""
     xyz: object
     feat: object
     normals: object = None
+    radius: object = None
+    beta: object = None
 
     def struct(self) -> adop_points:
         n, c = self.feat.shape
         assert tuple(self.xyz.shape) == (n, 3)
         return adop_points(n, c, dtype_code(self.feat.dtype), _dev_ptr(self.xyz), _dev_ptr(self.feat),
-                           _dev_ptr(self.normals))
+                           _dev_ptr(self.normals), _dev_ptr(self.radius), _dev_ptr(self.beta))
 
 
 @dataclass
@@ -158,9 +165,10 @@ class Params:
     znear: float = 1e-3
     background: object = None  # c float32 CUDA tensor or None
     flags: int = 0
+    gamma: float = 1.5         # stochastic discarding (with ADOP_FLAG_DISCARD)
 
     def struct(self) -> adop_params:
-        return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags)
+        return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags, self.gamma)
 
 
 def camera_struct(cam, crf_lut=None) -> adop_camera:
@@ -295,6 +303,20 @@ def _ws_ptr(ws):
     p = ws.data_ptr()
     a = (p + 255) // 256 * 256
     return ct.c_void_p(a), ws.numel() - (a - p)
+
+
+def adop_point_radius(xyz, k: int = 4, stream=None):
+    """Distance of every point to its k-th nearest other point (float32 CUDA
+    tensor), the world radius of stochastic point discarding (Sec. 3.1)."""
+    torch = _torch()
+    lib = load()
+    n = xyz.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=xyz.device)
+    nb = int(lib.adop_point_radius_workspace_bytes(n))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=xyz.device)
+    wp, wn = _ws_ptr(ws)
+    _check(lib.adop_point_radius(_dev_ptr(xyz.contiguous()), n, int(k), _dev_ptr(out), wp, wn, _stream_ptr(stream)))
+    return out
 
 
 def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):

@@ -77,16 +77,17 @@ def _effective_cameras(cameras, xi, intrinsics):
 
 class _Rasterize(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, xyz, feat, xi, intr, cams, params, out_dtype, keep_state, crf_luts):
+    def forward(ctx, xyz, feat, xi, intr, cams, params, out_dtype, keep_state, crf_luts, discard):
         dev = xyz.device
         levels = params.levels
-        pts = A.Points(xyz.contiguous(), feat.contiguous())
+        pts = A.Points(xyz.contiguous(), feat.contiguous(), None, *discard)
         frames = [A.Frame.alloc(c, feat.shape[1], levels, out_dtype, keep_state, dev,
                                 xyz.shape[0] if keep_state else None) for c in cams]
         ws = A.alloc_workspace(pts, cams, params, crf_luts, dev)
         A.adop_render_forward(pts, cams, params, frames, ws, crf_luts=crf_luts)
         ctx.save_for_backward(xyz, feat)
         ctx.frames, ctx.cams, ctx.params, ctx.ws, ctx.crf_luts = frames, cams, params, ws, crf_luts
+        ctx.discard = discard
         ctx.has_xi, ctx.has_intr = xi is not None, intr is not None
         ctx.xi_dev = None if xi is None else xi.device
         ctx.intr_dev = None if intr is None else intr.device
@@ -114,21 +115,26 @@ class _Rasterize(torch.autograd.Function):
         gpose = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
         gintr = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
         params = A.Params(ctx.params.levels, ctx.params.alpha, ctx.params.znear, ctx.params.background,
-                          ctx.params.flags | A.ADOP_FLAG_GRAD_ASSIGN)
-        pts = A.Points(xyz.contiguous(), feat.contiguous())
+                          ctx.params.flags | A.ADOP_FLAG_GRAD_ASSIGN, ctx.params.gamma)
+        pts = A.Points(xyz.contiguous(), feat.contiguous(), None, *ctx.discard)
         A.adop_render_backward(pts, ctx.cams, params, ctx.frames, gimgs, gfeat, gxyz, gpose, gintr, ctx.ws,
                                crf_luts=ctx.crf_luts)
         g_feat = None if gfeat is None else gfeat.to(feat.dtype)
         g_xi = None if not ctx.needs_input_grad[2] else gpose.to(ctx.xi_dev)
         g_intr = None if not ctx.needs_input_grad[3] else gintr.to(ctx.intr_dev)
-        return gxyz, g_feat, g_xi, g_intr, None, None, None, None, None
+        return gxyz, g_feat, g_xi, g_intr, None, None, None, None, None, None
 
 
 def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01, znear=1e-3, background=None,
-              flags=0, out_dtype=torch.float32, keep_state=True, crf_luts=None):
+              flags=0, out_dtype=torch.float32, keep_state=True, crf_luts=None, radius=None, beta=None, gamma=1.5):
     """Differentiable render of every camera; returns [camera][layer] images
-    (c x h_l x w_l).  See the module docstring for the gradients."""
+    (c x h_l x w_l).  See the module docstring for the gradients.  With
+    radius and beta (float32 per point), stochastic point discarding
+    (Eq. discard) with threshold gamma."""
     cams = _effective_cameras(cameras, xi, intrinsics)
-    params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN)
-    outs = _Rasterize.apply(xyz, feat, xi, intrinsics, cams, params, out_dtype, keep_state, crf_luts)
+    if radius is not None:
+        flags |= A.ADOP_FLAG_DISCARD
+    params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN, gamma)
+    outs = _Rasterize.apply(xyz, feat, xi, intrinsics, cams, params, out_dtype, keep_state, crf_luts,
+                            (radius, beta))
     return [list(outs[k * levels:(k + 1) * levels]) for k in range(len(cameras))]

@@ -174,6 +174,15 @@ __device__ __forceinline__ bool pixel_at(float u0, float v0, int l, int32_t w, i
   return pu >= 0 && pu < wl && pv >= 0 && pv < hl;
 }
 
+// Eq. discard (stochastic point discarding): keep the point at layer l iff
+// (t * t) * g2 > 1 - beta, t = (f32(fx 2^-l) * r_world) / z, g2 = f32(gamma^2):
+// the paper's r_screen / sqrt(1 - beta) > 1 / gamma without the square root,
+// with r_screen = fx r_world / (z 2^l).  Fixed FP32 order, no contraction.
+__device__ __forceinline__ bool discard_keep(const DevCam& cam, float z, float r, float beta, float g2, int l) {
+  const float t = __fdiv_rn(__fmul_rn(__fmul_rn(cam.fx, layer_scale(l)), r), z);
+  return __fmul_rn(__fmul_rn(t, t), g2) > __fsub_rn(1.0f, beta);
+}
+
 __device__ __forceinline__ unsigned long long depth_key(float z, int64_t i) {
   return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)(uint32_t)i;
 }

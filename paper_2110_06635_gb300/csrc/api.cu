@@ -151,8 +151,14 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
   if (!finite(prm->alpha) || prm->alpha < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   if (!finite(prm->znear) || prm->znear < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "znear must be finite and >= 0");
   if (prm->flags & ~(uint32_t)(ADOP_FLAG_NORMAL_CULL | ADOP_FLAG_GRAD_ALL_PROJECTED | ADOP_FLAG_EPILOGUE |
-                               ADOP_FLAG_GRAD_ASSIGN))
+                               ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD))
     return fail(ADOP_ERR_INVALID_ARG, "unknown flag bits 0x%x", prm->flags);
+  if (prm->flags & ADOP_FLAG_DISCARD) {
+    if (!(prm->gamma > 0.0f) || !finite(prm->gamma))
+      return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_DISCARD needs a finite gamma > 0");
+    if (pts->n > 0 && (!pts->radius || !pts->beta))
+      return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_DISCARD needs per-point radius and beta");
+  }
   if ((prm->flags & ADOP_FLAG_NORMAL_CULL) && pts->n > 0 && !pts->normals)
     return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_NORMAL_CULL needs normals");
   for (int k = 0; k < n_cam; ++k) {
@@ -254,6 +260,9 @@ PointArgs point_args(const adop_points* pts, const adop_params* prm, int ncam) {
   a.feat = pts->feat;
   a.normals = (prm->flags & ADOP_FLAG_NORMAL_CULL) ? pts->normals : nullptr;
   a.background = prm->background;
+  a.radius = (prm->flags & ADOP_FLAG_DISCARD) ? pts->radius : nullptr;
+  a.beta = (prm->flags & ADOP_FLAG_DISCARD) ? pts->beta : nullptr;
+  a.g2 = prm->gamma * prm->gamma;
   a.n = pts->n;
   a.levels = prm->levels;
   a.ncam = ncam;

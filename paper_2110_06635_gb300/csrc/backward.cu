@@ -256,8 +256,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
         bool loaded = false;
         float du0 = 0.0f, dv0 = 0.0f;
         bool spatial = false;
+        const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
         for (int l = 0; l < a.levels; ++l) {
           if (!((vmask >> l) & 1u) && !b.all_projected) continue;
+          if (a.radius && !discard_keep(cam, X2, rw, bt, a.g2, l)) continue;
           int32_t pu, pv;
           if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
           const int32_t wl = cam.w >> l, hl = cam.h >> l;

@@ -71,8 +71,10 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
     if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
     camera(cam, X0, X1, X2, u0, v0);
     const unsigned long long key = depth_key(X2, i);
+    const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
     for (int l = 0; l < a.levels; ++l) {
       int32_t pu, pv;
+      if (a.radius && !discard_keep(cam, X2, rw, bt, a.g2, l)) continue;
       if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
       unsigned long long* slot = cam.key[l] + (int64_t)pv * (cam.w >> l) + pu;
       if (key < __ldcg(slot)) atomicMin(slot, key);
@@ -98,12 +100,14 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
     if ((X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
       camera(cam, X0, X1, X2, u0, v0);
+      const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
       int64_t pix[kL];
       uint32_t zb[kL];
 #pragma unroll
       for (int l = 0; l < kL; ++l) {
         int32_t pu, pv;
-        pix[l] = (l < a.levels && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? (int64_t)pv * (cam.w >> l) + pu : -1;
+        const bool keep = l < a.levels && (!a.radius || discard_keep(cam, X2, rw, bt, a.g2, l));
+        pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? (int64_t)pv * (cam.w >> l) + pu : -1;
       }
 #pragma unroll
       for (int l = 0; l < kL; ++l)

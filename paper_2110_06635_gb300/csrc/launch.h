@@ -14,6 +14,9 @@ struct PointArgs {
   const void* feat;
   const float* normals;  // non-NULL only when normal culling is on
   const float* background;
+  const float* radius;  // stochastic discarding (NULL = off): world radius per point
+  const float* beta;    // and uniform draw per point
+  float g2;             // f32(gamma * gamma)
   int64_t n;
   int32_t levels;
   int32_t ncam;         // cameras in this launch (<= kMaxCamsPerLaunch)

@@ -201,6 +201,8 @@ void Server::launch_locked() {
     a.feat = P.feat;
     a.normals = (cfg.flags & ADOP_FLAG_NORMAL_CULL) ? P.normals : nullptr;
     a.background = cfg.background;
+    a.radius = nullptr;
+    a.beta = nullptr;
     a.n = P.n;
     a.levels = cfg.levels;
     a.ncam = (int32_t)pick.size();

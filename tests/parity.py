@@ -67,18 +67,20 @@ def to_np(t):
 
 def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, flags=0,
             grads=None, out_dtype="f32", keep_state=True, backward=True, normals=False, crf=True,
-            grad_assign=False, init=0.0, vis=True):
+            grad_assign=False, init=0.0, vis=True, discard=None):
     """Forward (+ backward) through the C ABI; returns numpy results."""
     import torch
     dev = "cuda"
     xyz = torch.from_numpy(scene.xyz).to(dev)
     feat = feat_tensor(scene, dtype, dev)
     nrm = torch.from_numpy(scene.normals).to(dev) if normals else None
-    pts = adop.Points(xyz, feat, nrm)
+    rad = None if discard is None else torch.from_numpy(discard[0]).to(dev)
+    bet = None if discard is None else torch.from_numpy(discard[1]).to(dev)
+    pts = adop.Points(xyz, feat, nrm, rad, bet)
     bg = None if background is None else torch.tensor(np.asarray(background, np.float32), device=dev)
     if grad_assign:
         flags |= adop.ADOP_FLAG_GRAD_ASSIGN
-    params = adop.Params(levels, alpha, znear, bg, flags)
+    params = adop.Params(levels, alpha, znear, bg, flags, 1.5 if discard is None else discard[2])
     luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(dev)
             if (crf and getattr(c, "crf", None) is not None) else None for c in cams]
     frames = [adop.Frame.alloc(c, scene.c, levels, torch_dtype(out_dtype), keep_state, dev,
@@ -108,7 +110,7 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
 
 
 def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
-               normals=False, epilogue=False, all_projected=False, backward=True):
+               normals=False, epilogue=False, all_projected=False, backward=True, discard=None):
     """The oracle on the same inputs: per camera forward (+ backward), summed
     over cameras for the per-point gradients."""
     feat = scene.feat_as(dtype)
@@ -116,8 +118,9 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
     dfeat = np.zeros((scene.n, scene.c))
     dxyz = np.zeros((scene.n, 3))
     for k, cam in enumerate(cams):
+        kw = {} if discard is None else {"radius": discard[0], "beta": discard[1], "gamma": discard[2]}
         f = orc.forward(scene.xyz, feat, cam, levels, alpha, znear, background,
-                        scene.normals if normals else None)
+                        scene.normals if normals else None, **kw)
         res["keys"].append(f.keys)
         res["cnt"].append(f.cnt)
         img = f.img.copy()
