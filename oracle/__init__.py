@@ -72,7 +72,9 @@ def _load():
                                      _P, _P, _P, _P, _P, _P, _P, _P]
         lib.orc_backward.restype = ct.c_int
         lib.orc_epilogue.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_double, _P, _P, _P,
-                                     _P, ct.c_int32, _P]
+                                     _P, ct.c_int32, ct.c_int32, _P]
+        lib.orc_photometric_grad.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, ct.c_double, _P, _P, _P,
+                                             _P, ct.c_int32, ct.c_int32, _P, _P]
         _lib = lib
     return _lib
 
@@ -265,9 +267,10 @@ def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_p
 
 
 def epilogue(img0, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0, 0.0), crf=None,
-             want_grad=False):
+             want_grad=False, leaky=False):
     """Sec. 3.3 photometric model on a layer-0 image (c x h x w, FP64).
-    Returns the new image (and d out / d in if want_grad)."""
+    Returns the new image (and d out / d in if want_grad).  leaky: the
+    training response curve of Eq. resonseleak."""
     lib = _load()
     img = np.array(img0, dtype=np.float64, copy=True, order="C")
     c, h, w = img.shape
@@ -276,8 +279,26 @@ def epilogue(img0, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0
     crf_n = 0 if crf is None else lut.shape[-1]
     lib.orc_epilogue(w, h, c, _ptr(img), ct.c_double(ev), _ptr(np.asarray(wb, np.float64)),
                      _ptr(np.asarray(vig_c, np.float64)), _ptr(np.asarray(vig_a, np.float64)),
-                     _ptr(lut), crf_n, _ptr(grad))
+                     _ptr(lut), crf_n, int(bool(leaky)), _ptr(grad))
     return (img, grad) if want_grad else img
+
+
+def photometric_grad(img0, G, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0, 0.0), crf=None,
+                     leaky=False):
+    """dL/d(EV, wb[3], c_v[2], a2, a4, a6) and dL/dLUT (3 x n) of the photometric
+    model (Sec. 3.3) on a layer-0 image before the epilogue, given dL/d(out)."""
+    lib = _load()
+    img = np.ascontiguousarray(img0, dtype=np.float64)
+    Gv = np.ascontiguousarray(G, dtype=np.float64)
+    c, h, w = img.shape
+    lut = None if crf is None else np.ascontiguousarray(crf, dtype=np.float64)
+    crf_n = 0 if crf is None else lut.shape[-1]
+    gp = np.zeros(9)
+    gcrf = np.zeros((3, max(crf_n, 1)))
+    lib.orc_photometric_grad(w, h, c, _ptr(img), _ptr(Gv), ct.c_double(ev), _ptr(np.asarray(wb, np.float64)),
+                             _ptr(np.asarray(vig_c, np.float64)), _ptr(np.asarray(vig_a, np.float64)), _ptr(lut),
+                             crf_n, int(bool(leaky)), _ptr(gp), _ptr(gcrf) if crf_n else None)
+    return gp, (gcrf if crf_n else None)
 
 
 from .bruteforce import bruteforce_render, bruteforce_spatial  # noqa: E402,F401

@@ -504,21 +504,52 @@ int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
 /* Photometric epilogue on layer 0 (Sec. 3.3)                           */
 /* ------------------------------------------------------------------ */
 
+/* Response curve R_ch(x) of one channel and its derivative.  crf_n < 2: the
+ * identity.  Otherwise a LUT of crf_n samples on [0,1] with linear
+ * interpolation; outside [0,1] the input is clamped (inference), or, with
+ * leaky != 0, the training response of Eq. resonseleak with alpha = 0.01:
+ * alpha x below 0 and -alpha / sqrt(x) + alpha + 1 above 1. */
+static double response(const double* lut, int32_t crf_n, int leaky, double x, double* dy, int32_t* seg,
+                       double* frac) {
+    *seg = -1;
+    *frac = 0.0;
+    if (crf_n < 2) {
+        *dy = 1.0;
+        return x;
+    }
+    const double a = 0.01;
+    if (leaky && x < 0.0) {
+        *dy = a;
+        return a * x;
+    }
+    if (leaky && x > 1.0) {
+        *dy = a / (2.0 * x * sqrt(x));
+        return -a / sqrt(x) + a + 1.0;
+    }
+    double xc = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+    double pos = xc * (crf_n - 1);
+    int32_t i0 = (int32_t)floor(pos);
+    if (i0 > crf_n - 2) i0 = crf_n - 2;
+    double f = pos - i0;
+    *seg = i0;
+    *frac = f;
+    *dy = (x < 0.0 || x > 1.0) ? 0.0 : (lut[i0 + 1] - lut[i0]) * (crf_n - 1);
+    return lut[i0] * (1.0 - f) + lut[i0 + 1] * f;
+}
+
 /*
  * In-place on the layer-0 planes of img (c x h x w), channels 0..min(c,3)-1:
  *   I_e = I / 2^EV                         (exposure)
  *   I_w = I_e * wb[ch]                     (white balance, multiplicative)
  *   I_v = I_w * (1 + a2 r^2 + a4 r^4 + a6 r^6),
  *         r = |(u/w, v/h) - c_v|           (vignette, normalised coords)
- *   out = R_ch(I_v)                        (response curve: LUT of crf_n
- *         samples on [0,1], linear interpolation, input clamped to [0,1])
- * If crf_n < 2 the response curve is the identity (no clamp).
+ *   out = R_ch(I_v)                        (response curve, see response())
  * If grad is not NULL it receives d out / d I per element (same layout), for
  * chaining an upstream gradient through the epilogue.
  */
 void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const double* wb,
                   const double* vig_c, const double* vig_a, const double* crf_lut, int32_t crf_n,
-                  double* grad) {
+                  int32_t leaky, double* grad) {
     const int64_t np = (int64_t)w * h;
     const int cc = c < 3 ? c : 3;
     const double e = pow(2.0, -ev);
@@ -532,17 +563,9 @@ void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const
                 double vig = 1.0 + vig_a[0] * r2 + vig_a[1] * r2 * r2 + vig_a[2] * r2 * r2 * r2;
                 double scale = e * wb[ch] * vig;
                 double x = img[(int64_t)ch * np + p] * scale;
-                double y = x, dy = 1.0;
-                if (crf_n >= 2) {
-                    const double* lut = crf_lut + (int64_t)ch * crf_n;
-                    double xc = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
-                    double pos = xc * (crf_n - 1);
-                    int32_t i0 = (int32_t)floor(pos);
-                    if (i0 > crf_n - 2) i0 = crf_n - 2;
-                    double f = pos - i0;
-                    y = lut[i0] * (1.0 - f) + lut[i0 + 1] * f;
-                    dy = (x < 0.0 || x > 1.0) ? 0.0 : (lut[i0 + 1] - lut[i0]) * (crf_n - 1);
-                }
+                double dy, f;
+                int32_t seg;
+                double y = response(crf_lut ? crf_lut + (int64_t)ch * crf_n : NULL, crf_n, leaky, x, &dy, &seg, &f);
                 img[(int64_t)ch * np + p] = y;
                 if (grad) grad[(int64_t)ch * np + p] = dy * scale;
             }
@@ -551,6 +574,59 @@ void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const
     if (grad)
         for (int ch = cc; ch < c; ++ch)
             for (int64_t p = 0; p < np; ++p) grad[(int64_t)ch * np + p] = 1.0;
+}
+
+/*
+ * Gradients of L with respect to the photometric parameters of one image
+ * (Sec. 3.3), given the layer-0 image before the epilogue (img, c x h x w)
+ * and dL/d(out) (G, same layout):
+ *   gp[0] dL/dEV, gp[1..3] dL/dwb, gp[4..5] dL/dc_v, gp[6..8] dL/d(a2, a4, a6)
+ *   gcrf[ch * crf_n + j] dL/dlut[ch][j] (NULL = not computed)
+ * Overwritten.  Sums in FP64.
+ */
+void orc_photometric_grad(int32_t w, int32_t h, int32_t c, const double* img, const double* G, double ev,
+                          const double* wb, const double* vig_c, const double* vig_a, const double* crf_lut,
+                          int32_t crf_n, int32_t leaky, double* gp, double* gcrf) {
+    const int64_t np = (int64_t)w * h;
+    const int cc = c < 3 ? c : 3;
+    const double e = pow(2.0, -ev);
+    for (int k = 0; k < 9; ++k) gp[k] = 0.0;
+    if (gcrf)
+        for (int64_t j = 0; j < 3 * (int64_t)crf_n; ++j) gcrf[j] = 0.0;
+    for (int ch = 0; ch < cc; ++ch) {
+        for (int32_t v = 0; v < h; ++v) {
+            for (int32_t u = 0; u < w; ++u) {
+                int64_t p = (int64_t)v * w + u;
+                double ru = (double)u / w - vig_c[0];
+                double rv = (double)v / h - vig_c[1];
+                double r2 = ru * ru + rv * rv;
+                double vig = 1.0 + vig_a[0] * r2 + vig_a[1] * r2 * r2 + vig_a[2] * r2 * r2 * r2;
+                double I = img[(int64_t)ch * np + p];
+                double x = I * e * wb[ch] * vig;
+                double dy, f;
+                int32_t seg;
+                response(crf_lut ? crf_lut + (int64_t)ch * crf_n : NULL, crf_n, leaky, x, &dy, &seg, &f);
+                double g = G[(int64_t)ch * np + p];
+                double gx = g * dy; /* dL/dx */
+                gp[0] += gx * x * (-log(2.0));
+                gp[1 + ch] += gx * I * e * vig;
+                /* dvig/dr2 and dr2/dc_v = -2 (p - c_v) */
+                double dvig = vig_a[0] + 2.0 * vig_a[1] * r2 + 3.0 * vig_a[2] * r2 * r2;
+                double base = gx * I * e * wb[ch];
+                gp[4] += base * dvig * (-2.0 * ru);
+                gp[5] += base * dvig * (-2.0 * rv);
+                gp[6] += base * r2;
+                gp[7] += base * r2 * r2;
+                gp[8] += base * r2 * r2 * r2;
+                if (gcrf && crf_n >= 2) {
+                    if (seg >= 0) {
+                        gcrf[ch * crf_n + seg] += g * (1.0 - f);
+                        gcrf[ch * crf_n + seg + 1] += g * f;
+                    }
+                }
+            }
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ */
