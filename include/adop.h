@@ -73,7 +73,9 @@ typedef struct {
  *   with r = |(u / w, v / h) - vig_c|; out = R_ch(I_v), R_ch a piecewise-linear
  *   LUT of crf_n samples on [0,1] (input clamped to [0,1]) at
  *   crf_lut[ch * crf_n ...] (device pointer, 3 x crf_n floats), or the identity
- *   if crf_lut is NULL. */
+ *   if crf_lut is NULL.  With ADOP_FLAG_LEAKY_CRF (training) the LUT response
+ *   leaks outside [0,1] as in Eq. resonseleak, alpha = 0.01: 0.01 x below 0,
+ *   -0.01 / sqrt(x) + 1.01 above 1. */
 typedef struct {
     float ev;
     float wb[3];
@@ -113,6 +115,7 @@ typedef struct {
 #define ADOP_FLAG_EPILOGUE (1u << 2)          /* apply the photometric model (fwd and bwd) */
 #define ADOP_FLAG_GRAD_ASSIGN (1u << 3)       /* grad_feat / grad_xyz are overwritten, not += */
 #define ADOP_FLAG_DISCARD (1u << 4)           /* stochastic point discarding, Eq. discard */
+#define ADOP_FLAG_LEAKY_CRF (1u << 5)         /* training response curve, Eq. resonseleak */
 
 /* levels: pyramid layers L (1..ADOP_MAX_LEVELS); alpha: fuzzy depth-test
  * threshold of Eq. depthtest (the paper uses 0.01); znear: points with
@@ -299,6 +302,23 @@ adop_status adop_serve_get_stats(adop_server* s, adop_serve_stats* out);
 adop_status adop_serve_reset_stats(adop_server* s);
 /* Cancel queued requests, finish admitted ones, free everything. */
 adop_status adop_serve_destroy(adop_server* s);
+
+/*
+ * Gradients of the photometric parameters (Sec. 3.3) of every camera whose
+ * epilogue is enabled (ADOP_FLAG_EPILOGUE and ph.enabled), from dL/d(out) of
+ * layer 0 (grad_image0[k]: c x h x w FP32, NULL = zero) and the layer-0 image
+ * before the epilogue, which is the forward's kept state (frames must carry
+ * key/count/acc).  Accumulated (+=):
+ *   grad_photo  n_cam x 9: dL/d(ev, wb[0..2], vig_c[0..1], vig_a[0..2])
+ *   grad_crf    dL/d(crf_lut): for each camera in order, 3 x its crf_n floats
+ *               (no entries for a camera without a LUT); NULL = not computed
+ * crf_n <= 4000.  Workspace: adop_photometric_workspace_bytes(n_cam).
+ */
+size_t adop_photometric_workspace_bytes(int32_t n_cam);
+adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, const adop_params* params,
+                                      int32_t c, const adop_frame* frames, const float* const* grad_image0,
+                                      float* grad_photo, float* grad_crf, void* workspace,
+                                      size_t workspace_bytes, adop_stream stream);
 
 /* Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by a pair of CUDA events recorded on the launch's stream (a few

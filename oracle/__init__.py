@@ -74,7 +74,7 @@ def _load():
         lib.orc_epilogue.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_double, _P, _P, _P,
                                      _P, ct.c_int32, ct.c_int32, _P]
         lib.orc_photometric_grad.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, ct.c_double, _P, _P, _P,
-                                             _P, ct.c_int32, ct.c_int32, _P, _P]
+                                             _P, ct.c_int32, ct.c_int32, _P, _P, _P]
         _lib = lib
     return _lib
 
@@ -284,7 +284,7 @@ def epilogue(img0, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0
 
 
 def photometric_grad(img0, G, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_a=(0.0, 0.0, 0.0), crf=None,
-                     leaky=False):
+                     leaky=False, with_abs=False):
     """dL/d(EV, wb[3], c_v[2], a2, a4, a6) and dL/dLUT (3 x n) of the photometric
     model (Sec. 3.3) on a layer-0 image before the epilogue, given dL/d(out)."""
     lib = _load()
@@ -293,12 +293,13 @@ def photometric_grad(img0, G, ev=0.0, wb=(1.0, 1.0, 1.0), vig_c=(0.5, 0.5), vig_
     c, h, w = img.shape
     lut = None if crf is None else np.ascontiguousarray(crf, dtype=np.float64)
     crf_n = 0 if crf is None else lut.shape[-1]
-    gp = np.zeros(9)
+    gp, gabs = np.zeros(9), np.zeros(9)
     gcrf = np.zeros((3, max(crf_n, 1)))
     lib.orc_photometric_grad(w, h, c, _ptr(img), _ptr(Gv), ct.c_double(ev), _ptr(np.asarray(wb, np.float64)),
                              _ptr(np.asarray(vig_c, np.float64)), _ptr(np.asarray(vig_a, np.float64)), _ptr(lut),
-                             crf_n, int(bool(leaky)), _ptr(gp), _ptr(gcrf) if crf_n else None)
-    return gp, (gcrf if crf_n else None)
+                             crf_n, int(bool(leaky)), _ptr(gp), _ptr(gcrf) if crf_n else None, _ptr(gabs))
+    out = (gp, (gcrf if crf_n else None))
+    return out + (gabs,) if with_abs else out
 
 
 from .bruteforce import bruteforce_render, bruteforce_spatial  # noqa: E402,F401

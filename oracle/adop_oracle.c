@@ -582,15 +582,16 @@ void orc_epilogue(int32_t w, int32_t h, int32_t c, double* img, double ev, const
  * and dL/d(out) (G, same layout):
  *   gp[0] dL/dEV, gp[1..3] dL/dwb, gp[4..5] dL/dc_v, gp[6..8] dL/d(a2, a4, a6)
  *   gcrf[ch * crf_n + j] dL/dlut[ch][j] (NULL = not computed)
+ *   gp_abs  the sum of |term| of each gp entry (error scale)
  * Overwritten.  Sums in FP64.
  */
 void orc_photometric_grad(int32_t w, int32_t h, int32_t c, const double* img, const double* G, double ev,
                           const double* wb, const double* vig_c, const double* vig_a, const double* crf_lut,
-                          int32_t crf_n, int32_t leaky, double* gp, double* gcrf) {
+                          int32_t crf_n, int32_t leaky, double* gp, double* gcrf, double* gp_abs) {
     const int64_t np = (int64_t)w * h;
     const int cc = c < 3 ? c : 3;
     const double e = pow(2.0, -ev);
-    for (int k = 0; k < 9; ++k) gp[k] = 0.0;
+    for (int k = 0; k < 9; ++k) gp[k] = gp_abs[k] = 0.0;
     if (gcrf)
         for (int64_t j = 0; j < 3 * (int64_t)crf_n; ++j) gcrf[j] = 0.0;
     for (int ch = 0; ch < cc; ++ch) {
@@ -608,16 +609,16 @@ void orc_photometric_grad(int32_t w, int32_t h, int32_t c, const double* img, co
                 response(crf_lut ? crf_lut + (int64_t)ch * crf_n : NULL, crf_n, leaky, x, &dy, &seg, &f);
                 double g = G[(int64_t)ch * np + p];
                 double gx = g * dy; /* dL/dx */
-                gp[0] += gx * x * (-log(2.0));
-                gp[1 + ch] += gx * I * e * vig;
                 /* dvig/dr2 and dr2/dc_v = -2 (p - c_v) */
                 double dvig = vig_a[0] + 2.0 * vig_a[1] * r2 + 3.0 * vig_a[2] * r2 * r2;
                 double base = gx * I * e * wb[ch];
-                gp[4] += base * dvig * (-2.0 * ru);
-                gp[5] += base * dvig * (-2.0 * rv);
-                gp[6] += base * r2;
-                gp[7] += base * r2 * r2;
-                gp[8] += base * r2 * r2 * r2;
+                double t[9] = {gx * x * (-log(2.0)), 0.0, 0.0, 0.0, base * dvig * (-2.0 * ru),
+                               base * dvig * (-2.0 * rv), base * r2, base * r2 * r2, base * r2 * r2 * r2};
+                t[1 + ch] = gx * I * e * vig;
+                for (int k = 0; k < 9; ++k) {
+                    gp[k] += t[k];
+                    gp_abs[k] += fabs(t[k]);
+                }
                 if (gcrf && crf_n >= 2) {
                     if (seg >= 0) {
                         gcrf[ch * crf_n + seg] += g * (1.0 - f);

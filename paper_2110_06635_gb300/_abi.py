@@ -21,6 +21,7 @@ ADOP_FLAG_GRAD_ALL_PROJECTED = 1 << 1
 ADOP_FLAG_EPILOGUE = 1 << 2
 ADOP_FLAG_GRAD_ASSIGN = 1 << 3
 ADOP_FLAG_DISCARD = 1 << 4
+ADOP_FLAG_LEAKY_CRF = 1 << 5
 ADOP_F32, ADOP_BF16, ADOP_F16 = 0, 1, 2
 
 STATUS = {0: "ADOP_OK", 1: "ADOP_ERR_INVALID_ARG", 2: "ADOP_ERR_UNSUPPORTED", 3: "ADOP_ERR_OUT_OF_MEMORY",
@@ -84,6 +85,8 @@ SIGNATURES = {
     "adop_render_backward_noalloc": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "adop_point_radius_workspace_bytes": (ct.c_size_t, [ct.c_int64]),
     "adop_point_radius": (ct.c_int, [_P, ct.c_int64, ct.c_int32, _P, _P, ct.c_size_t, _P]),
+    "adop_photometric_workspace_bytes": (ct.c_size_t, [ct.c_int32]),
+    "adop_photometric_backward": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32, _P, _P, _P, _P, _P, ct.c_size_t, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
     "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
 }
@@ -317,6 +320,24 @@ def adop_point_radius(xyz, k: int = 4, stream=None):
     wp, wn = _ws_ptr(ws)
     _check(lib.adop_point_radius(_dev_ptr(xyz.contiguous()), n, int(k), _dev_ptr(out), wp, wn, _stream_ptr(stream)))
     return out
+
+
+def adop_photometric_backward(cams, params: Params, c: int, frames, grad_image0, grad_photo, grad_crf=None,
+                              stream=None, crf_luts=None):
+    """Gradients of the photometric parameters (Sec. 3.3), accumulated into
+    grad_photo (n_cam x 9: ev, wb[3], vig_c[2], vig_a[3]) and grad_crf (the
+    LUTs' gradients, camera after camera) from dL/d(layer-0 image)."""
+    torch = _torch()
+    lib = load()
+    pr = params.struct()
+    arr = _cams_array(cams, crf_luts)
+    fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
+    g0 = (ct.c_void_p * len(cams))(*[_dev_ptr(g) for g in grad_image0])
+    nb = int(lib.adop_photometric_workspace_bytes(len(cams)))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=grad_photo.device)
+    wp, wn = _ws_ptr(ws)
+    _check(lib.adop_photometric_backward(arr, len(cams), ct.byref(pr), int(c), fr, g0, _dev_ptr(grad_photo),
+                                         _dev_ptr(grad_crf), wp, wn, _stream_ptr(stream)))
 
 
 def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):

@@ -56,19 +56,26 @@ def se3_exp(xi) -> np.ndarray:
     return T
 
 
+def apply_tangent(cam, xi):
+    """The camera with its pose replaced by exp(xi) (R, t) (Eq. tangent): the
+    update applied after an optimiser step on the tangent, which is then
+    reset to zero."""
+    T = np.eye(4)
+    T[:3, :3] = np.asarray(cam.R, np.float64)
+    T[:3, 3] = np.asarray(cam.t, np.float64)
+    T = se3_exp(np.asarray(xi, np.float64)) @ T
+    c = copy.copy(cam)
+    c.R = T[:3, :3].astype(np.float32)
+    c.t = T[:3, 3].astype(np.float32)
+    return c
+
+
 def _effective_cameras(cameras, xi, intrinsics):
     cams = []
     xi_h = None if xi is None else xi.detach().to("cpu", torch.float64).numpy()
     k_h = None if intrinsics is None else intrinsics.detach().to("cpu", torch.float64).numpy()
     for k, cam in enumerate(cameras):
-        c = copy.copy(cam)
-        if xi_h is not None and np.any(xi_h[k] != 0):
-            T = np.eye(4)
-            T[:3, :3] = np.asarray(cam.R, np.float64)
-            T[:3, 3] = np.asarray(cam.t, np.float64)
-            T = se3_exp(xi_h[k]) @ T
-            c.R = T[:3, :3].astype(np.float32)
-            c.t = T[:3, 3].astype(np.float32)
+        c = apply_tangent(cam, xi_h[k]) if xi_h is not None and np.any(xi_h[k] != 0) else copy.copy(cam)
         if k_h is not None:
             c.fx, c.fy, c.cx, c.cy, c.k1, c.k2 = (float(v) for v in k_h[k])
         cams.append(c)

@@ -45,6 +45,7 @@ struct DevCam {
   int32_t* bin_list;         // visible point indices, tile by tile (NULL: no binning)
   // photometric epilogue (Sec. 3.3); ev_scale = 2^-EV, computed on the host
   int32_t epi;
+  int32_t leaky;  // training response curve (Eq. resonseleak) instead of clamping
   int32_t crf_n;
   float ev_scale;
   float wb[3];
@@ -260,8 +261,46 @@ __device__ __forceinline__ int layer_of(const DevCam& cam, int levels, int64_t g
   return l;
 }
 
+// Response curve of channel ch at x (Sec. 3.3): the LUT of crf_n samples on
+// [0,1] with linear interpolation, the input clamped to [0,1] -- or, in
+// training (cam.leaky), leaking outside it as in Eq. resonseleak with
+// alpha = 0.01 -- and the identity without a LUT.  *slope = dR/dx; *seg and
+// *frac: the LUT segment and the weight of its upper sample (seg = -1: no LUT
+// sample is used).
+__device__ __forceinline__ float response(const DevCam& cam, int ch, float x, float* slope, int* seg, float* frac) {
+  *seg = -1;
+  *frac = 0.0f;
+  if (cam.crf == nullptr || cam.crf_n < 2) {
+    *slope = 1.0f;
+    return x;
+  }
+  constexpr float kLeak = 0.01f;
+  if (cam.leaky && x < 0.0f) {
+    *slope = kLeak;
+    return kLeak * x;
+  }
+  if (cam.leaky && x > 1.0f) {
+    const float rs = rsqrtf(x);
+    *slope = 0.5f * kLeak * rs / x;
+    return -kLeak * rs + kLeak + 1.0f;
+  }
+  const int n = cam.crf_n;
+  const float xc = fminf(fmaxf(x, 0.0f), 1.0f);
+  const float pos = xc * (float)(n - 1);
+  const int i0 = min((int)floorf(pos), n - 2);
+  const float fr = pos - (float)i0;
+  const float* lut = cam.crf + ch * n;
+  const float lo = __ldg(lut + i0), hi = __ldg(lut + i0 + 1);
+  *seg = i0;
+  *frac = fr;
+  *slope = (x < 0.0f || x > 1.0f) ? 0.0f : (hi - lo) * (float)(n - 1);
+  return lo * (1.0f - fr) + hi * fr;
+}
+
 // Photometric model of Sec. 3.3 on one value of channel ch at layer-0 pixel
-// (u, v); if dydx is given it receives d out / d in.
+// (u, v): exposure 2^-EV, white balance, vignette 1 + a2 r^2 + a4 r^4 + a6 r^6
+// with r = |(u/w, v/h) - c_v|, then the response curve.  If dydx is given it
+// receives d out / d in.
 __device__ __forceinline__ float epilogue(const DevCam& cam, int ch, int32_t u, int32_t v, float x,
                                           float* dydx) {
   const float ru = __fdiv_rn((float)u, (float)cam.w) - cam.vig_c[0];
@@ -269,21 +308,10 @@ __device__ __forceinline__ float epilogue(const DevCam& cam, int ch, int32_t u, 
   const float r2 = ru * ru + rv * rv;
   const float vig = 1.0f + r2 * (cam.vig_a[0] + r2 * (cam.vig_a[1] + r2 * cam.vig_a[2]));
   const float scale = cam.ev_scale * cam.wb[ch] * vig;
-  const float xs = x * scale;
-  float y = xs, dy = 1.0f;
-  if (cam.crf != nullptr && cam.crf_n >= 2) {
-    const int n = cam.crf_n;
-    const float xc = fminf(fmaxf(xs, 0.0f), 1.0f);
-    const float pos = xc * (float)(n - 1);
-    int i0 = (int)floorf(pos);
-    i0 = min(i0, n - 2);
-    const float fr = pos - (float)i0;
-    const float* lut = cam.crf + ch * n;
-    const float a = __ldg(lut + i0), b = __ldg(lut + i0 + 1);
-    y = a * (1.0f - fr) + b * fr;
-    dy = (xs < 0.0f || xs > 1.0f) ? 0.0f : (b - a) * (float)(n - 1);
-  }
-  if (dydx) *dydx = dy * scale;
+  float slope, frac;
+  int seg;
+  const float y = response(cam, ch, x * scale, &slope, &seg, &frac);
+  if (dydx) *dydx = slope * scale;
   return y;
 }
 

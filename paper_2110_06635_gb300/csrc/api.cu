@@ -151,7 +151,7 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
   if (!finite(prm->alpha) || prm->alpha < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   if (!finite(prm->znear) || prm->znear < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "znear must be finite and >= 0");
   if (prm->flags & ~(uint32_t)(ADOP_FLAG_NORMAL_CULL | ADOP_FLAG_GRAD_ALL_PROJECTED | ADOP_FLAG_EPILOGUE |
-                               ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD))
+                               ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD | ADOP_FLAG_LEAKY_CRF))
     return fail(ADOP_ERR_INVALID_ARG, "unknown flag bits 0x%x", prm->flags);
   if (prm->flags & ADOP_FLAG_DISCARD) {
     if (!(prm->gamma > 0.0f) || !finite(prm->gamma))
@@ -334,6 +334,7 @@ void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_
   d.tiles = d.tiles_x * tiles_along(d.h);
   const adop_photometric& ph = cam.ph;
   d.epi = ((flags & ADOP_FLAG_EPILOGUE) && ph.enabled) ? 1 : 0;
+  d.leaky = (flags & ADOP_FLAG_LEAKY_CRF) ? 1 : 0;
   d.ev_scale = (float)std::exp2(-(double)ph.ev);
   for (int j = 0; j < 3; ++j) {
     d.wb[j] = ph.wb[j];

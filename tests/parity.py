@@ -110,7 +110,7 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
 
 
 def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
-               normals=False, epilogue=False, all_projected=False, backward=True, discard=None):
+               normals=False, epilogue=False, all_projected=False, backward=True, discard=None, leaky=False):
     """The oracle on the same inputs: per camera forward (+ backward), summed
     over cameras for the per-point gradients."""
     feat = scene.feat_as(dtype)
@@ -128,7 +128,7 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
         if epilogue and getattr(cam, "epilogue", False):
             c, h, w = scene.c, cam.h, cam.w
             img0, dgain = orc.epilogue(f.img[:c * h * w].reshape(c, h, w), cam.ev, cam.wb, cam.vig_c, cam.vig_a,
-                                       cam.crf, want_grad=True)
+                                       cam.crf, want_grad=True, leaky=leaky)
             img[:c * h * w] = img0.ravel()
             if G is not None:
                 G = G.copy()
