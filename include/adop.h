@@ -116,6 +116,8 @@ typedef struct {
 #define ADOP_FLAG_GRAD_ASSIGN (1u << 3)       /* grad_feat / grad_xyz are overwritten, not += */
 #define ADOP_FLAG_DISCARD (1u << 4)           /* stochastic point discarding, Eq. discard */
 #define ADOP_FLAG_LEAKY_CRF (1u << 5)         /* training response curve, Eq. resonseleak */
+#define ADOP_FLAG_LOG_DESCRIPTORS (1u << 6)   /* tau stored as log values: exp(tau) is blended (Sec. 3.2);
+                                                 grad_feat is then dL/dtau of the stored values */
 
 /* levels: pyramid layers L (1..ADOP_MAX_LEVELS); alpha: fuzzy depth-test
  * threshold of Eq. depthtest (the paper uses 0.01); znear: points with

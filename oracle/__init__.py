@@ -61,14 +61,14 @@ def _load():
         lib.orc_pyramid_pixels.argtypes = [ct.c_int32, ct.c_int32, ct.c_int]
         lib.orc_pyramid_pixels.restype = ct.c_int64
         lib.orc_forward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P, ct.c_int32, ct.c_float,
-                                    ct.c_float, _P, _P, _P, ct.c_float, _P, _P, _P, _P, _P]
+                                    ct.c_float, _P, _P, _P, ct.c_float, ct.c_int32, _P, _P, _P, _P, _P]
         lib.orc_knn_radius.argtypes = [ct.c_int64, _P, ct.c_int32, _P]
         lib.orc_forward.restype = ct.c_int
         lib.orc_project_jac_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.orc_camera_f64.argtypes = [_P, _P, _P]
         lib.orc_camera_f64_many.argtypes = [ct.c_int64, _P, _P, _P]
         lib.orc_backward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, ct.c_int32, ct.c_float,
-                                     _P, ct.c_int32, _P, _P, _P, _P, _P, _P,
+                                     _P, ct.c_int32, ct.c_int32, _P, _P, _P, _P, _P, _P,
                                      _P, _P, _P, _P, _P, _P, _P, _P]
         lib.orc_backward.restype = ct.c_int
         lib.orc_epilogue.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_double, _P, _P, _P,
@@ -201,7 +201,7 @@ def knn_radius(xyz, k: int = 4) -> np.ndarray:
 
 
 def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None,
-            radius=None, beta=None, gamma=1.5) -> Forward:
+            radius=None, beta=None, gamma=1.5, log_desc=False) -> Forward:
     """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend);
     with radius/beta, stochastic point discarding (Eq. discard) at every layer."""
     lib = _load()
@@ -222,7 +222,7 @@ def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, n
     K, T = _intr(cam), _pose(cam)
     rc = lib.orc_forward(n, _ptr(xyz), c, _ptr(f64), _ptr(nrm), ct.byref(K), ct.byref(T), int(levels),
                          ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(rad), _ptr(bet), ct.c_float(gamma),
-                         _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
+                         int(bool(log_desc)), _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
     if rc != 0:
         raise MemoryError("oracle forward: allocation failed")
     return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)
@@ -240,7 +240,8 @@ class Backward:
     gv: np.ndarray
 
 
-def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_projected=False) -> Backward:
+def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_projected=False,
+             log_desc=False) -> Backward:
     """Sec. 3.1's backward pass for one camera; G is dL/dI over the
     concatenated pyramid (same layout as ``fwd.img``)."""
     lib = _load()
@@ -257,7 +258,7 @@ def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_p
     bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
     K, T = _intr(cam), _pose(cam)
     rc = lib.orc_backward(n, _ptr(xyz), c, _ptr(f64), ct.byref(K), ct.byref(T), fwd.levels,
-                          ct.c_float(alpha), _ptr(bg), int(bool(all_projected)), _ptr(fwd.keys),
+                          ct.c_float(alpha), _ptr(bg), int(bool(all_projected)), int(bool(log_desc)), _ptr(fwd.keys),
                           _ptr(fwd.cnt), _ptr(fwd.img), _ptr(fwd.pix), _ptr(fwd.z), _ptr(G),
                           _ptr(dfeat), _ptr(dxyz), _ptr(dpose), _ptr(dintr), _ptr(dpa), _ptr(dia),
                           _ptr(gu), _ptr(gv))

@@ -217,9 +217,18 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
 int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, const float* normals,
                 const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
                 float znear, const double* background,
-                const float* radius, const float* beta, float gamma,
+                const float* radius, const float* beta, float gamma, int32_t log_desc,
                 uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out) {
     int64_t npx = orc_pyramid_pixels(K->w, K->h, levels);
+    /* Logarithmic descriptors (Sec. 3.2) are converted to linear values before
+     * blending. */
+    double* lin = NULL;
+    if (log_desc) {
+        lin = (double*)malloc(sizeof(double) * (size_t)(n * c + 1));
+        if (!lin) return -1;
+        for (int64_t j = 0; j < n * c; ++j) lin[j] = exp(feat[j]);
+        feat = lin;
+    }
     int32_t* pix = pix_out ? pix_out : (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * levels + 1));
     float* zf = z_out ? z_out : (float*)malloc(sizeof(float) * (size_t)(n + 1));
     double* sum = (double*)calloc((size_t)(npx * c + 1), sizeof(double));
@@ -276,6 +285,7 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
         }
     }
     free(sum);
+    free(lin);
     if (!pix_out) free(pix);
     if (!z_out) free(zf);
     return 0;
@@ -383,7 +393,7 @@ void orc_project_jac_f64(const orc_intrinsics* K, const orc_pose* T, const float
  */
 int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
                  const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
-                 const double* background, int32_t all_projected,
+                 const double* background, int32_t all_projected, int32_t log_desc,
                  const uint64_t* keys, const uint32_t* cnt, const double* img,
                  const int32_t* pix, const float* zf, const double* G,
                  double* dfeat, double* dxyz, double* dpose, double* dintr,
@@ -391,6 +401,14 @@ int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
     const float a1 = 1.0f + alpha;
     double* D = (double*)malloc(sizeof(double) * (size_t)(c > 0 ? c : 1));
     if (!D) return -1;
+    const double* feat_stored = feat;
+    double* lin = NULL;
+    if (log_desc) { /* blend and induced changes act on exp(tau) (Sec. 3.2) */
+        lin = (double*)malloc(sizeof(double) * (size_t)(n * c + 1));
+        if (!lin) return -1;
+        for (int64_t j = 0; j < n * c; ++j) lin[j] = exp(feat_stored[j]);
+        feat = lin;
+    }
     for (int k = 0; k < 6; ++k) dpose[k] = dintr[k] = dpose_abs[k] = dintr_abs[k] = 0.0;
     for (int64_t i = 0; i < n * c; ++i) dfeat[i] = 0.0;
     for (int64_t i = 0; i < n * 3; ++i) dxyz[i] = 0.0;
@@ -496,6 +514,9 @@ int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
             }
         }
     }
+    if (log_desc) /* d exp(tau) / d tau = exp(tau) */
+        for (int64_t j = 0; j < n * c; ++j) dfeat[j] *= lin[j];
+    free(lin);
     free(D);
     return 0;
 }

@@ -22,6 +22,7 @@ ADOP_FLAG_EPILOGUE = 1 << 2
 ADOP_FLAG_GRAD_ASSIGN = 1 << 3
 ADOP_FLAG_DISCARD = 1 << 4
 ADOP_FLAG_LEAKY_CRF = 1 << 5
+ADOP_FLAG_LOG_DESCRIPTORS = 1 << 6
 ADOP_F32, ADOP_BF16, ADOP_F16 = 0, 1, 2
 
 STATUS = {0: "ADOP_OK", 1: "ADOP_ERR_INVALID_ARG", 2: "ADOP_ERR_UNSUPPORTED", 3: "ADOP_ERR_OUT_OF_MEMORY",

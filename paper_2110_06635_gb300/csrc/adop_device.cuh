@@ -235,6 +235,17 @@ __device__ __forceinline__ void load_feat(const T* __restrict__ feat, int64_t i,
   }
 }
 
+// The descriptors of point i as linear FP32 values: stored values, or exp of
+// them for logarithmic descriptors (converted during rasterization, Sec. 3.2).
+template <int C, typename T>
+__device__ __forceinline__ void load_desc(const T* __restrict__ feat, int64_t i, bool log_desc, float (&f)[C]) {
+  load_feat<C, T>(feat, i, f);
+  if (log_desc) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) f[k] = expf(f[k]);
+  }
+}
+
 // acc[0..C) += f (FP32), as few global atomics as the alignment allows
 // (sm_90+ has float2/float4 vector atomics on global memory).
 template <int C>

@@ -151,7 +151,8 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
   if (!finite(prm->alpha) || prm->alpha < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   if (!finite(prm->znear) || prm->znear < 0.0f) return fail(ADOP_ERR_INVALID_ARG, "znear must be finite and >= 0");
   if (prm->flags & ~(uint32_t)(ADOP_FLAG_NORMAL_CULL | ADOP_FLAG_GRAD_ALL_PROJECTED | ADOP_FLAG_EPILOGUE |
-                               ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD | ADOP_FLAG_LEAKY_CRF))
+                               ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD | ADOP_FLAG_LEAKY_CRF |
+                               ADOP_FLAG_LOG_DESCRIPTORS))
     return fail(ADOP_ERR_INVALID_ARG, "unknown flag bits 0x%x", prm->flags);
   if (prm->flags & ADOP_FLAG_DISCARD) {
     if (!(prm->gamma > 0.0f) || !finite(prm->gamma))
@@ -263,6 +264,7 @@ PointArgs point_args(const adop_points* pts, const adop_params* prm, int ncam) {
   a.radius = (prm->flags & ADOP_FLAG_DISCARD) ? pts->radius : nullptr;
   a.beta = (prm->flags & ADOP_FLAG_DISCARD) ? pts->beta : nullptr;
   a.g2 = prm->gamma * prm->gamma;
+  a.log_desc = (prm->flags & ADOP_FLAG_LOG_DESCRIPTORS) ? 1 : 0;
   a.n = pts->n;
   a.levels = prm->levels;
   a.ncam = ncam;

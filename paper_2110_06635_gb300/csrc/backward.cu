@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
           }
           if (!(vis || b.all_projected) || !spatial_out) continue;
           if (!loaded) {
-            load_feat<C, TF>(feat, i, tau);
+            load_desc<C, TF>(feat, i, a.log_desc, tau);
             loaded = true;
           }
           float g_u, g_v;
@@ -290,6 +290,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
         if (spatial && (du0 != 0.0f || dv0 != 0.0f)) {
           chain_rule(cam, X0, X1, X2, du0, dv0, red, gx);
           touched = true;
+        }
+        if (a.log_desc && touched) {  // d exp(tau) / d tau = exp(tau)
+          if (!loaded) load_desc<C, TF>(feat, i, true, tau);
+#pragma unroll
+          for (int k = 0; k < C; ++k) gf[k] *= tau[k];
         }
       }
     }
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       transform(cam, __ldcs(a.xyz + 3 * i), __ldcs(a.xyz + 3 * i + 1), __ldcs(a.xyz + 3 * i + 2), X0, X1, X2);
       camera(cam, X0, X1, X2, u0, v0);
       float tau[C];
-      load_feat<C, TF>(feat, i, tau);
+      load_desc<C, TF>(feat, i, a.log_desc, tau);
       pt[lane * PS + 0] = X2;
       pt[lane * PS + 1] = u0;
       pt[lane * PS + 2] = v0;
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
     if (i < a.n) {
       float gf[C];
 #pragma unroll
-      for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k];
+      for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k] * (a.log_desc && mask ? pt[lane * PS + 3 + k] : 1.0f);
       // (binned: the points in no Lambda were already given zero gradients)
       float gx[3] = {0.0f, 0.0f, 0.0f};
       const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
       for (int l = 0; l < kL; ++l) {
         if (pix[l] < 0 || !(X2 <= __fmul_rn(__uint_as_float(zb[l]), a.a1))) continue;
         if (!loaded) {
-          load_feat<C, TF>(feat, i, f);
+          load_desc<C, TF>(feat, i, a.log_desc, f);
           loaded = true;
         }
         atomic_add_vec<C>(cam.acc + (cam.off[l] + pix[l]) * C, f);

@@ -17,6 +17,7 @@ struct PointArgs {
   const float* radius;  // stochastic discarding (NULL = off): world radius per point
   const float* beta;    // and uniform draw per point
   float g2;             // f32(gamma * gamma)
+  int32_t log_desc;     // descriptors are stored as log values: blend exp(tau)
   int64_t n;
   int32_t levels;
   int32_t ncam;         // cameras in this launch (<= kMaxCamsPerLaunch)

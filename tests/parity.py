@@ -110,7 +110,8 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
 
 
 def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
-               normals=False, epilogue=False, all_projected=False, backward=True, discard=None, leaky=False):
+               normals=False, epilogue=False, all_projected=False, backward=True, discard=None, leaky=False,
+               log_desc=False):
     """The oracle on the same inputs: per camera forward (+ backward), summed
     over cameras for the per-point gradients."""
     feat = scene.feat_as(dtype)
@@ -119,6 +120,7 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
     dxyz = np.zeros((scene.n, 3))
     for k, cam in enumerate(cams):
         kw = {} if discard is None else {"radius": discard[0], "beta": discard[1], "gamma": discard[2]}
+        kw["log_desc"] = log_desc
         f = orc.forward(scene.xyz, feat, cam, levels, alpha, znear, background,
                         scene.normals if normals else None, **kw)
         res["keys"].append(f.keys)
@@ -135,7 +137,7 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
                 G[:c * h * w] *= dgain.ravel()
         res["img"].append(img)
         if backward and G is not None:
-            b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected)
+            b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected, log_desc)
             dfeat += b.dfeat
             dxyz += b.dxyz
             for key in ("dpose", "dintr", "dpose_abs", "dintr_abs"):

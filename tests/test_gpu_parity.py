@@ -168,3 +168,15 @@ def test_alpha_zero_and_large_alpha(adop, orc, tiny):
         g = gpu_run(adop, sc, cams, "f32", alpha=alpha, grads=G)
         r = oracle_run(orc, sc, cams, "f32", alpha=alpha, grads=G)
         compare(g, r)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_log_descriptors(adop, orc, tiny, dtype):
+    """Logarithmic descriptors (Sec. 3.2): exp(tau) is blended; dL/dtau of the stored values."""
+    sc, cams = tiny
+    sc = scenes.Scene(sc.xyz, (sc.feat * 0.5).astype(np.float32), sc.normals)
+    G = _grads(cams, sc.c, 4, 13)
+    for vis in (True, False):
+        g = gpu_run(adop, sc, cams, dtype, grads=G, flags=adop.ADOP_FLAG_LOG_DESCRIPTORS, vis=vis)
+        r = oracle_run(orc, sc, cams, dtype, grads=G, log_desc=True)
+        compare(g, r, dtype)

@@ -245,3 +245,28 @@ def test_normal_culling_literal(orc):
     nrm = np.array([[0, 0, 1.0], [0, 0, -1.0]], np.float32)
     f = orc.forward(xyz, np.ones((2, 1)), cam, levels=1, normals=nrm)
     assert f.pix[:, 0].tolist() == [1, -1]
+
+
+def test_log_descriptors(orc):
+    """Logarithmic descriptors (Sec. 3.2) are blended as exp(tau): the render
+    of log(F) with conversion equals the render of F, and dL/dtau is the
+    linear gradient times exp(tau) -- checked by central differences."""
+    sc, cam = _small_sphere_view(n=1200)
+    F = np.exp(np.random.default_rng(5).normal(scale=0.7, size=(sc.n, sc.c)))
+    a = orc.forward(sc.xyz, np.log(F), cam, log_desc=True)
+    b = orc.forward(sc.xyz, F, cam)
+    assert np.array_equal(a.keys, b.keys) and np.allclose(a.img, b.img, rtol=1e-12, atol=1e-12)
+    G = np.random.default_rng(6).normal(size=a.img.shape)
+    ga = orc.backward(a, sc.xyz, np.log(F), cam, G, log_desc=True)
+    gb = orc.backward(b, sc.xyz, F, cam, G)
+    assert np.allclose(ga.dfeat, gb.dfeat * F, rtol=1e-12, atol=1e-12)
+    assert np.allclose(ga.dxyz, gb.dxyz, rtol=1e-9, atol=1e-9)
+    tau = np.log(F)
+    rng = np.random.default_rng(7)
+    for i in rng.choice(np.nonzero(np.abs(ga.dfeat).sum(1))[0], 10, replace=False):
+        for ch in range(sc.c):
+            tp, tm = tau.copy(), tau.copy()
+            tp[i, ch] += 1e-6
+            tm[i, ch] -= 1e-6
+            fd = (G @ orc.forward(sc.xyz, tp, cam, log_desc=True).img - G @ orc.forward(sc.xyz, tm, cam, log_desc=True).img) / 2e-6
+            assert np.isclose(fd, ga.dfeat[i, ch], rtol=1e-5, atol=1e-7)
