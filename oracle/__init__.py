@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 
 class _Intr(ct.Structure):
     _fields_ = [("w", ct.c_int32), ("h", ct.c_int32)] + [
-        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")]
+        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")] + [("model", ct.c_int32)]
 
 
 class _Pose(ct.Structure):
@@ -56,6 +56,8 @@ def _load():
     if _lib is None:
         lib = ct.CDLL(build())
         lib.orc_project_f32.argtypes = [_P, _P, _P, _P, _P, _P]
+        lib.orc_project_f32.restype = ct.c_int
+        lib.orc_camera_fisheye_f64.argtypes = [_P, _P, _P]
         lib.orc_pixel.argtypes = [ct.c_float, ct.c_float, ct.c_int, ct.c_int32, ct.c_int32, _P, _P]
         lib.orc_pixel.restype = ct.c_int
         lib.orc_pyramid_pixels.argtypes = [ct.c_int32, ct.c_int32, ct.c_int]
@@ -66,7 +68,7 @@ def _load():
         lib.orc_forward.restype = ct.c_int
         lib.orc_project_jac_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.orc_camera_f64.argtypes = [_P, _P, _P]
-        lib.orc_camera_f64_many.argtypes = [ct.c_int64, _P, _P, _P]
+        lib.orc_camera_f64_many.argtypes = [ct.c_int64, _P, _P, _P, ct.c_int32]
         lib.orc_backward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, ct.c_int32, ct.c_float,
                                      _P, ct.c_int32, ct.c_int32, _P, _P, _P, _P, _P, _P,
                                      _P, _P, _P, _P, _P, _P, _P, _P]
@@ -85,7 +87,8 @@ def _ptr(a):
 
 def _intr(cam) -> _Intr:
     return _Intr(int(cam.w), int(cam.h), *[float(getattr(cam, k)) for k in
-                                           ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
+                                           ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")],
+                 int(getattr(cam, "model", 0)))
 
 
 def _pose(cam) -> _Pose:
@@ -139,6 +142,16 @@ def project_jac_f64(cam, x):
     return uv, X, JX.reshape(2, 3), JK.reshape(2, 6)
 
 
+def camera_fisheye_f64(k9, X):
+    """The fisheye model (stereographic + radial polynomial) in FP64."""
+    lib = _load()
+    k = np.ascontiguousarray(k9, dtype=np.float64).reshape(9)
+    Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(3)
+    uv = np.zeros(2)
+    lib.orc_camera_fisheye_f64(_ptr(k), _ptr(Xv), _ptr(uv))
+    return uv
+
+
 def camera_f64(k9, X):
     """The camera model in FP64: k9 = (fx, fy, cx, cy, k1, k2, k3, p1, p2),
     X camera-space point -> (u0, v0)."""
@@ -150,13 +163,13 @@ def camera_f64(k9, X):
     return uv
 
 
-def camera_f64_many(k9, X):
-    """camera_f64 over an n x 3 array of camera-space points -> n x 2."""
+def camera_f64_many(k9, X, model=0):
+    """camera_f64 (or the fisheye model) over an n x 3 array of camera-space points -> n x 2."""
     lib = _load()
     k = np.ascontiguousarray(k9, dtype=np.float64).reshape(9)
     Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
     uv = np.zeros((Xv.shape[0], 2))
-    lib.orc_camera_f64_many(Xv.shape[0], _ptr(k), _ptr(Xv), _ptr(uv))
+    lib.orc_camera_f64_many(Xv.shape[0], _ptr(k), _ptr(Xv), _ptr(uv), int(model))
     return uv
 
 

@@ -43,13 +43,17 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* Camera model C: pinhole with Brown-Conrady distortion (k1,k2,k3 radial,
- * p1,p2 tangential).  The paper's scenes use "Pinhole + Dist." (Table
- * scenes) without stating the distortion polynomial; this is the common
- * five-coefficient model. */
+/* Camera model C.  model 0: pinhole with Brown-Conrady distortion (k1,k2,k3
+ * radial, p1,p2 tangential); the paper's scenes use "Pinhole + Dist." (Table
+ * scenes) without stating the polynomial; this is the common
+ * five-coefficient model.  model 1: fisheye (the paper's Office scene; its
+ * formula is not given), read as the stereographic projection r = 2 tan(theta/2)
+ * with the same radial polynomial in r^2 (p1, p2 unused), and -- as the paper
+ * prescribes for a model without a z -- the distance to the camera as depth. */
 typedef struct {
     int32_t w, h;
     float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+    int32_t model;
 } orc_intrinsics;
 
 /* World-to-camera rigid transform (R, t), R row-major (Eq. render). */
@@ -73,8 +77,26 @@ static void transform_f32(const orc_pose* T, const float* x, float* X) {
 }
 
 /* Camera model C applied to a camera-space point; returns layer-0 pixel
- * coordinates (u0, v0).  z = X[2] is the depth of Eq. depthtest. */
-static void camera_f32(const orc_intrinsics* K, const float* X, float* u0, float* v0) {
+ * coordinates (u0, v0) and the depth of Eq. depthtest (pinhole: z = X[2];
+ * fisheye: the distance |X|).  Returns 0 where the model is undefined
+ * (fisheye: on the negative optical axis). */
+static int camera_f32(const orc_intrinsics* K, const float* X, float* u0, float* v0, float* depth) {
+    if (K->model == 1) {
+        /* stereographic: normalised radius 2 tan(theta/2) = 2 rho / (|X| + Z) */
+        float d = sqrtf((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
+        float s = d + X[2];
+        *depth = d;
+        if (!(s > 0.0f)) return 0;
+        float a = 2.0f / s;
+        float xn = a * X[0];
+        float yn = a * X[1];
+        float r2 = xn * xn + yn * yn;
+        float dd = 1.0f + r2 * (K->k1 + r2 * (K->k2 + r2 * K->k3));
+        *u0 = K->fx * (xn * dd) + K->cx;
+        *v0 = K->fy * (yn * dd) + K->cy;
+        return 1;
+    }
+    *depth = X[2];
     float xn = X[0] / X[2];
     float yn = X[1] / X[2];
     float r2 = xn * xn + yn * yn;
@@ -86,15 +108,16 @@ static void camera_f32(const orc_intrinsics* K, const float* X, float* u0, float
     float yd = yn * d + ty;
     *u0 = K->fx * xd + K->cx;
     *v0 = K->fy * yd + K->cy;
+    return 1;
 }
 
-/* Exported: the FP32 contract for one point (used by the projection pins). */
-void orc_project_f32(const orc_intrinsics* K, const orc_pose* T, const float* x,
-                     float* u0, float* v0, float* z) {
+/* Exported: the FP32 contract for one point (used by the projection pins).
+ * Returns 0 where the camera model is undefined. */
+int orc_project_f32(const orc_intrinsics* K, const orc_pose* T, const float* x,
+                    float* u0, float* v0, float* z) {
     float X[3];
     transform_f32(T, x, X);
-    camera_f32(K, X, u0, v0);
-    *z = X[2];
+    return camera_f32(K, X, u0, v0, z);
 }
 
 /* Eq. round + Eq. boundscheck for layer l.  The layer scale 2^-l is exact.
@@ -167,12 +190,11 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
                         const float* radius, const float* beta, float gamma,
                         int32_t* pix, float* zf) {
     for (int64_t i = 0; i < n; ++i) {
-        float X[3], u0, v0;
+        float X[3], u0 = 0.0f, v0 = 0.0f, z;
         transform_f32(T, xyz + 3 * i, X);
-        camera_f32(K, X, &u0, &v0);
-        float z = X[2];
+        int defined = camera_f32(K, X, &u0, &v0, &z);
         zf[i] = z;
-        int keep = (z > znear);
+        int keep = defined && (z > znear);
         if (keep && normals) {
             const float* nn = normals + 3 * i;
             float Rn[3];
@@ -318,9 +340,26 @@ void orc_camera_f64(const double* k9, const double* X, double* uv) {
     uv[1] = fy * yd + cy;
 }
 
-/* orc_camera_f64 over n camera-space points (X: n x 3, uv: n x 2). */
-void orc_camera_f64_many(int64_t n, const double* k9, const double* X, double* uv) {
-    for (int64_t i = 0; i < n; ++i) orc_camera_f64(k9, X + 3 * i, uv + 2 * i);
+/* The fisheye model (stereographic + radial polynomial) in FP64, k9 as above. */
+void orc_camera_fisheye_f64(const double* k9, const double* X, double* uv) {
+    const double d = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    const double a = 2.0 / (d + X[2]);
+    const double xn = a * X[0], yn = a * X[1];
+    const double r2 = xn * xn + yn * yn;
+    const double dd = 1.0 + k9[4] * r2 + k9[5] * r2 * r2 + k9[6] * r2 * r2 * r2;
+    uv[0] = k9[0] * xn * dd + k9[2];
+    uv[1] = k9[1] * yn * dd + k9[3];
+}
+
+/* orc_camera_f64 (model 0) or orc_camera_fisheye_f64 (model 1) over n
+ * camera-space points (X: n x 3, uv: n x 2). */
+void orc_camera_f64_many(int64_t n, const double* k9, const double* X, double* uv, int32_t model) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (model == 1)
+            orc_camera_fisheye_f64(k9, X + 3 * i, uv + 2 * i);
+        else
+            orc_camera_f64(k9, X + 3 * i, uv + 2 * i);
+    }
 }
 
 void orc_project_jac_f64(const orc_intrinsics* K, const orc_pose* T, const float* x,
@@ -330,6 +369,37 @@ void orc_project_jac_f64(const orc_intrinsics* K, const orc_pose* T, const float
                (double)T->R[3 * r + 2] * x[2] + (double)T->t[r];
     }
     const double k9[9] = {K->fx, K->fy, K->cx, K->cy, K->k1, K->k2, K->k3, K->p1, K->p2};
+    if (K->model == 1) {
+        orc_camera_fisheye_f64(k9, X, uv);
+        const double fx = K->fx, fy = K->fy, k1 = K->k1, k2 = K->k2, k3 = K->k3;
+        const double d = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+        const double s = d + X[2];
+        const double a = 2.0 / s;
+        const double xn = a * X[0], yn = a * X[1];
+        const double r2 = xn * xn + yn * yn;
+        const double dd = 1.0 + k1 * r2 + k2 * r2 * r2 + k3 * r2 * r2 * r2;
+        const double ddr = k1 + 2.0 * k2 * r2 + 3.0 * k3 * r2 * r2;
+        /* d s / d X = X / d + e_z ; d a / d X = -2 / s^2 * d s / d X */
+        double ds[3] = {X[0] / d, X[1] / d, X[2] / d + 1.0};
+        double da[3];
+        for (int k = 0; k < 3; ++k) da[k] = -2.0 / (s * s) * ds[k];
+        double dxn[3], dyn[3];
+        for (int k = 0; k < 3; ++k) {
+            dxn[k] = X[0] * da[k] + (k == 0 ? a : 0.0);
+            dyn[k] = X[1] * da[k] + (k == 1 ? a : 0.0);
+        }
+        const double dxd_dxn = dd + xn * ddr * 2.0 * xn, dxd_dyn = xn * ddr * 2.0 * yn;
+        const double dyd_dxn = yn * ddr * 2.0 * xn, dyd_dyn = dd + yn * ddr * 2.0 * yn;
+        for (int k = 0; k < 3; ++k) {
+            J_X[k] = fx * (dxd_dxn * dxn[k] + dxd_dyn * dyn[k]);
+            J_X[3 + k] = fy * (dyd_dxn * dxn[k] + dyd_dyn * dyn[k]);
+        }
+        J_K[0] = xn * dd; J_K[1] = 0.0; J_K[2] = 1.0; J_K[3] = 0.0;
+        J_K[4] = fx * xn * r2; J_K[5] = fx * xn * r2 * r2;
+        J_K[6] = 0.0; J_K[7] = yn * dd; J_K[8] = 0.0; J_K[9] = 1.0;
+        J_K[10] = fy * yn * r2; J_K[11] = fy * yn * r2 * r2;
+        return;
+    }
     orc_camera_f64(k9, X, uv);
     const double fx = K->fx, fy = K->fy;
     const double k1 = K->k1, k2 = K->k2, k3 = K->k3, p1 = K->p1, p2 = K->p2;

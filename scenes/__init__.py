@@ -49,6 +49,7 @@ class Camera:
     vig_a: tuple = (0.0, 0.0, 0.0)
     crf: np.ndarray | None = None  # 3 x n LUT on [0,1] or None
     epilogue: bool = False         # apply the photometric model to this view
+    model: int = 0                 # 0 pinhole + Brown-Conrady, 1 fisheye (stereographic)
 
     def with_pose(self, R, t) -> "Camera":
         return replace(self, R=np.asarray(R, np.float32), t=np.asarray(t, np.float32))

@@ -26,18 +26,22 @@ def _hat(xi):
     return M
 
 
-def _scene():
+def _scene(model=0):
     sc = tiny_spheres(2500, 3, seed=21)
     from scipy.spatial.transform import Rotation
     R = Rotation.from_rotvec([0.05, -0.1, 0.02]).as_matrix().astype(np.float32)
-    cam = Camera(80, 60, 64.0, 62.0, 40.5, 29.5, k1=0.05, k2=-0.02, k3=0.004, p1=0.003, p2=-0.002,
-                 R=R, t=np.array([-0.4, -0.3, 2.2], np.float32))
+    if model == 1:  # a wide fisheye close to the spheres
+        cam = Camera(96, 80, 30.0, 30.0, 48.5, 40.5, k1=0.05, k2=-0.02, k3=0.004, R=R,
+                     t=np.array([-0.4, -0.3, 0.9], np.float32), model=1)
+    else:
+        cam = Camera(80, 60, 64.0, 62.0, 40.5, 29.5, k1=0.05, k2=-0.02, k3=0.004, p1=0.003, p2=-0.002,
+                     R=R, t=np.array([-0.4, -0.3, 2.2], np.float32))
     return sc, cam
 
 
-@pytest.fixture(scope="module")
-def grads(orc):
-    sc, cam = _scene()
+@pytest.fixture(scope="module", params=[0, 1], ids=["pinhole", "fisheye"])
+def grads(orc, request):
+    sc, cam = _scene(request.param)
     f = orc.forward(sc.xyz, sc.feat, cam)
     G = np.random.default_rng(22).normal(size=f.img.shape)
     b = orc.backward(f, sc.xyz, sc.feat, cam, G)
@@ -52,9 +56,9 @@ def _k9(cam):
                      ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
 
 
-def _surrogate(orc, k9, R, t, xyz, wu, wv):
+def _surrogate(orc, k9, R, t, xyz, wu, wv, model=0):
     X = xyz @ R.T + t
-    uv = orc.camera_f64_many(k9, X)
+    uv = orc.camera_f64_many(k9, X, model)
     return float(wu @ uv[:, 0] + wv @ uv[:, 1])
 
 
@@ -76,8 +80,8 @@ def test_position_gradient(orc, grads):
             xp, xm = xyz[i:i + 1].copy(), xyz[i:i + 1].copy()
             xp[0, k] += h
             xm[0, k] -= h
-            fd = (_surrogate(orc, k9, R, t, xp, wu[i:i + 1], wv[i:i + 1])
-                  - _surrogate(orc, k9, R, t, xm, wu[i:i + 1], wv[i:i + 1])) / (2 * h)
+            fd = (_surrogate(orc, k9, R, t, xp, wu[i:i + 1], wv[i:i + 1], cam.model)
+                  - _surrogate(orc, k9, R, t, xm, wu[i:i + 1], wv[i:i + 1], cam.model)) / (2 * h)
             assert np.isclose(fd, b.dxyz[i, k], rtol=1e-6, atol=1e-6 * np.abs(b.dxyz[i]).max())
 
 
@@ -95,7 +99,7 @@ def test_pose_gradient_left_increment(orc, grads):
             xi = np.zeros(6)
             xi[k] = s * h
             Tp = expm(_hat(xi)) @ T
-            vals.append(_surrogate(orc, k9, Tp[:3, :3], Tp[:3, 3], xyz, wu, wv))
+            vals.append(_surrogate(orc, k9, Tp[:3, :3], Tp[:3, 3], xyz, wu, wv, cam.model))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - b.dpose[k]) <= 1e-6 * b.dpose_abs[k], (k, fd, b.dpose[k])
 
@@ -111,5 +115,6 @@ def test_intrinsics_gradient(orc, grads):
         kp, km = k9.copy(), k9.copy()
         kp[k] += h
         km[k] -= h
-        fd = (_surrogate(orc, kp, R, t, xyz, wu, wv) - _surrogate(orc, km, R, t, xyz, wu, wv)) / (2 * h)
+        fd = (_surrogate(orc, kp, R, t, xyz, wu, wv, cam.model)
+              - _surrogate(orc, km, R, t, xyz, wu, wv, cam.model)) / (2 * h)
         assert abs(fd - b.dintr[k]) <= 1e-6 * b.dintr_abs[k], (k, fd, b.dintr[k])
