@@ -51,14 +51,22 @@ typedef enum {
 
 typedef enum { ADOP_F32 = 0, ADOP_BF16 = 1, ADOP_F16 = 2 } adop_dtype;
 
-/* Camera model C of Eq. render: pinhole with Brown-Conrady distortion.
+/* Camera model C of Eq. render.
+ * model 0, pinhole with Brown-Conrady distortion ("Pinhole + Dist."):
  *   xn = X/Z, yn = Y/Z, r2 = xn^2 + yn^2, d = 1 + r2 (k1 + r2 (k2 + r2 k3))
  *   xd = xn d + 2 p1 xn yn + p2 (r2 + 2 xn^2), yd = yn d + p1 (r2 + 2 yn^2) + 2 p2 xn yn
- *   u0 = fx xd + cx, v0 = fy yd + cy, and layer l uses (u0, v0) / 2^l.
+ *   depth = Z.
+ * model 1, fisheye (the paper's Office scene; no formula is given -- read as
+ * the stereographic projection, r = 2 tan(theta / 2)):
+ *   a = 2 / (|X| + Z), (xn, yn) = a (X, Y), xd = xn d, yd = yn d (d as above,
+ *   p1, p2 unused); depth = |X| (the paper's rule for a model without z);
+ *   undefined on the negative optical axis.
+ * Then u0 = fx xd + cx, v0 = fy yd + cy, and layer l uses (u0, v0) / 2^l.
  * w, h: layer-0 image size in pixels (1 .. 16384). */
 typedef struct {
     int32_t w, h;
     float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+    int32_t model;
 } adop_intrinsics;
 
 /* World-to-camera rigid transform (R, t) of Eq. render; X = R x + t, R row-major. */

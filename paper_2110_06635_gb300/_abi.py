@@ -37,7 +37,7 @@ class AdopError(RuntimeError):
 
 class adop_intrinsics(ct.Structure):
     _fields_ = [("w", ct.c_int32), ("h", ct.c_int32)] + [
-        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")]
+        (k, ct.c_float) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")] + [("model", ct.c_int32)]
 
 
 class adop_pose(ct.Structure):
@@ -180,7 +180,8 @@ def camera_struct(cam, crf_lut=None) -> adop_camera:
     t; optionally ev, wb, vig_c, vig_a and epilogue) into adop_camera.
     crf_lut: 3 x n float32 CUDA tensor of the response curve, or None."""
     K = adop_intrinsics(int(cam.w), int(cam.h), *[float(getattr(cam, k, 0.0)) for k in
-                                                  ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
+                                                  ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")],
+                        int(getattr(cam, "model", 0)))
     R = np.asarray(cam.R, np.float32).reshape(9)
     t = np.asarray(cam.t, np.float32).reshape(3)
     T = adop_pose((ct.c_float * 9)(*R.tolist()), (ct.c_float * 3)(*t.tolist()))

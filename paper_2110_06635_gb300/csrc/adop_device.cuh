@@ -29,6 +29,7 @@ struct DevCam {
   float t[3];
   float fx, fy, cx, cy, k1, k2, k3, p1, p2;
   int32_t w, h;
+  int32_t model;  // 0 pinhole + Brown-Conrady, 1 fisheye (stereographic)
   int64_t off[ADOP_MAX_LEVELS + 1];  // first pixel of each layer in the concatenated pyramid
   unsigned long long* key[ADOP_MAX_LEVELS];
   uint32_t* cnt[ADOP_MAX_LEVELS];
@@ -128,9 +129,28 @@ __device__ __forceinline__ void transform(const DevCam& cam, float x0, float x1,
                            __fmul_rn(cam.R[8], x2)), cam.t[2]);
 }
 
-// Camera model C: layer-0 pixel coordinates of a camera-space point.
-__device__ __forceinline__ void camera(const DevCam& cam, float X0, float X1, float X2, float& u0,
-                                       float& v0) {
+// Camera model C: layer-0 pixel coordinates (u0, v0) of a camera-space point
+// and its depth for the depth test -- z for the pinhole, the distance |X|
+// for the fisheye (the paper's rule for a model without a z).  Returns false
+// where the model is undefined (fisheye: the negative optical axis).
+__device__ __forceinline__ bool camera(const DevCam& cam, float X0, float X1, float X2, float& u0, float& v0,
+                                       float& depth) {
+  if (cam.model == 1) {
+    // stereographic: normalised radius 2 tan(theta/2) = 2 rho / (|X| + Z)
+    const float d = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(X0, X0), __fmul_rn(X1, X1)), __fmul_rn(X2, X2)));
+    const float s = __fadd_rn(d, X2);
+    depth = d;
+    if (!(s > 0.0f)) return false;
+    const float a = __fdiv_rn(2.0f, s);
+    const float xn = __fmul_rn(a, X0), yn = __fmul_rn(a, X1);
+    const float r2 = __fadd_rn(__fmul_rn(xn, xn), __fmul_rn(yn, yn));
+    const float dd = __fadd_rn(
+        1.0f, __fmul_rn(r2, __fadd_rn(cam.k1, __fmul_rn(r2, __fadd_rn(cam.k2, __fmul_rn(r2, cam.k3))))));
+    u0 = __fadd_rn(__fmul_rn(cam.fx, __fmul_rn(xn, dd)), cam.cx);
+    v0 = __fadd_rn(__fmul_rn(cam.fy, __fmul_rn(yn, dd)), cam.cy);
+    return true;
+  }
+  depth = X2;
   const float xn = __fdiv_rn(X0, X2);
   const float yn = __fdiv_rn(X1, X2);
   const float r2 = __fadd_rn(__fmul_rn(xn, xn), __fmul_rn(yn, yn));
@@ -145,6 +165,7 @@ __device__ __forceinline__ void camera(const DevCam& cam, float X0, float X1, fl
   const float yd = __fadd_rn(__fmul_rn(yn, d), ty);
   u0 = __fadd_rn(__fmul_rn(cam.fx, xd), cam.cx);
   v0 = __fadd_rn(__fmul_rn(cam.fy, yd), cam.cy);
+  return true;
 }
 
 // Eq. normalculling as printed: keep iff (R n)^T (R x + t) > 0.

@@ -168,6 +168,8 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
       return fail(ADOP_ERR_INVALID_ARG, "camera %d: image size %dx%d outside [1, 16384]", k, K.w, K.h);
     if ((K.w >> (prm->levels - 1)) < 1 || (K.h >> (prm->levels - 1)) < 1)
       return fail(ADOP_ERR_INVALID_ARG, "camera %d: %dx%d too small for %d levels", k, K.w, K.h, prm->levels);
+    if (K.model != 0 && K.model != 1)
+      return fail(ADOP_ERR_INVALID_ARG, "camera %d: unknown camera model %d", k, K.model);
     const float kv[9] = {K.fx, K.fy, K.cx, K.cy, K.k1, K.k2, K.k3, K.p1, K.p2};
     for (float v : kv)
       if (!finite(v)) return fail(ADOP_ERR_INVALID_ARG, "camera %d: non-finite intrinsics", k);
@@ -331,6 +333,7 @@ void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_
   d.k1 = cam.K.k1; d.k2 = cam.K.k2; d.k3 = cam.K.k3; d.p1 = cam.K.p1; d.p2 = cam.K.p2;
   d.w = cam.K.w;
   d.h = cam.K.h;
+  d.model = cam.K.model;
   pyramid_pixels(d.w, d.h, levels, d.off);
   d.tiles_x = tiles_along(d.w);
   d.tiles = d.tiles_x * tiles_along(d.h);

@@ -88,6 +88,39 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
 // position (dL/dx = R^T dL/dX).  FP32.
 __device__ __forceinline__ void chain_rule(const DevCam& cam, float X0, float X1, float X2, float du0, float dv0,
                                            float (&red)[12], float (&gx)[3]) {
+  if (cam.model == 1) {
+    // fisheye (stereographic): a = 2 / (|X| + Z), (xn, yn) = a (X, Y)
+    const float d = sqrtf(X0 * X0 + X1 * X1 + X2 * X2);
+    const float s = d + X2;
+    const float a = 2.0f / s;
+    const float xn = a * X0, yn = a * X1;
+    const float r2 = xn * xn + yn * yn;
+    const float dd = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
+    const float ddr = cam.k1 + r2 * (2.0f * cam.k2 + 3.0f * cam.k3 * r2);
+    const float gxd = cam.fx * du0, gyd = cam.fy * dv0;
+    // through (xd, yd) = (xn, yn) dd(r2)
+    const float gxn = gxd * (dd + 2.0f * xn * xn * ddr) + gyd * (2.0f * xn * yn * ddr);
+    const float gyn = gxd * (2.0f * xn * yn * ddr) + gyd * (dd + 2.0f * yn * yn * ddr);
+    // (xn, yn) = a (X0, X1), da/dX = -2/s^2 (X/d + e_z)
+    const float c = -2.0f / (s * s) * (gxn * X0 + gyn * X1);
+    const float dX0 = gxn * a + c * X0 / d, dX1 = gyn * a + c * X1 / d, dX2 = c * (X2 / d + 1.0f);
+    red[0] += dX0;
+    red[1] += dX1;
+    red[2] += dX2;
+    red[3] += X1 * dX2 - X2 * dX1;
+    red[4] += X2 * dX0 - X0 * dX2;
+    red[5] += X0 * dX1 - X1 * dX0;
+    red[6] += du0 * xn * dd;
+    red[7] += dv0 * yn * dd;
+    red[8] += du0;
+    red[9] += dv0;
+    red[10] += (gxd * xn + gyd * yn) * r2;
+    red[11] += (gxd * xn + gyd * yn) * r2 * r2;
+    gx[0] = cam.R[0] * dX0 + cam.R[3] * dX1 + cam.R[6] * dX2;
+    gx[1] = cam.R[1] * dX0 + cam.R[4] * dX1 + cam.R[7] * dX2;
+    gx[2] = cam.R[2] * dX0 + cam.R[5] * dX1 + cam.R[8] * dX2;
+    return;
+  }
   const float iz = 1.0f / X2;
   const float xn = X0 * iz, yn = X1 * iz;
   const float r2 = xn * xn + yn * yn;
@@ -247,11 +280,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
     // accumulate pass; without the record every in-bounds layer is examined
     const uint32_t vmask = cam.vis ? (cam.vis[i] & 0xFFu) : 0xFFu;
     if (vmask != 0u || b.all_projected) {
-      float X0, X1, X2, u0, v0;
+      float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd;
       transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-      const bool valid = (X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2));
+      const bool valid = camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) &&
+                         !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2));
       if (valid) {
-        camera(cam, X0, X1, X2, u0, v0);
         float tau[C];
         bool loaded = false;
         float du0 = 0.0f, dv0 = 0.0f;
@@ -259,14 +292,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
         const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
         for (int l = 0; l < a.levels; ++l) {
           if (!((vmask >> l) & 1u) && !b.all_projected) continue;
-          if (a.radius && !discard_keep(cam, X2, rw, bt, a.g2, l)) continue;
+          if (a.radius && !discard_keep(cam, zd, rw, bt, a.g2, l)) continue;
           int32_t pu, pv;
           if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
           const int32_t wl = cam.w >> l, hl = cam.h >> l;
           const int64_t base = cam.off[l];
           const int64_t gp = base + (int64_t)pv * wl + pu;
           const float4 ip = __ldg(info + gp);
-          const bool vis = cam.vis ? (((vmask >> l) & 1u) != 0u) : (X2 <= __fmul_rn(ip.x, a.a1));
+          const bool vis = cam.vis ? (((vmask >> l) & 1u) != 0u) : (zd <= __fmul_rn(ip.x, a.a1));
           if (vis) {
             // dI(p)/dtau_i = 1/|Lambda(p)| for every member of Lambda(p)
             float G[GS];
@@ -281,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
             loaded = true;
           }
           float g_u, g_v;
-          spatial_grad<C>(cam, info, base, pu, pv, wl, hl, X2, a.a1, tau, g_u, g_v, pol);
+          spatial_grad<C>(cam, info, base, pu, pv, wl, hl, zd, a.a1, tau, g_u, g_v, pol);
           const float sc = layer_scale(l);
           du0 = fmaf(g_u, sc, du0);
           dv0 = fmaf(g_v, sc, dv0);
@@ -344,12 +377,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
     const uint32_t mask = i < a.n ? (__ldcs(cam.vis + i) & 0xFFu) : 0u;
     float X0 = 0.f, X1 = 0.f, X2 = 1.f;
     if (mask) {
-      float u0, v0;
+      float u0 = 0.0f, v0 = 0.0f, zd = 0.0f;
       transform(cam, __ldcs(a.xyz + 3 * i), __ldcs(a.xyz + 3 * i + 1), __ldcs(a.xyz + 3 * i + 2), X0, X1, X2);
-      camera(cam, X0, X1, X2, u0, v0);
+      camera(cam, X0, X1, X2, u0, v0, zd);  // defined: the point passed a fuzzy test
       float tau[C];
       load_desc<C, TF>(feat, i, a.log_desc, tau);
-      pt[lane * PS + 0] = X2;
+      pt[lane * PS + 0] = zd;
       pt[lane * PS + 1] = u0;
       pt[lane * PS + 2] = v0;
 #pragma unroll

@@ -65,16 +65,15 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
                                                     const __grid_constant__ PointArgs a) {
   const DevCam& cam = cams.c[blockIdx.y];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    float X0, X1, X2, u0, v0;
+    float X0, X1, X2, u0, v0, zd;
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-    if (!(X2 > a.znear)) continue;
+    if (!camera(cam, X0, X1, X2, u0, v0, zd) || !(zd > a.znear)) continue;
     if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
-    camera(cam, X0, X1, X2, u0, v0);
-    const unsigned long long key = depth_key(X2, i);
+    const unsigned long long key = depth_key(zd, i);
     const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
     for (int l = 0; l < a.levels; ++l) {
       int32_t pu, pv;
-      if (a.radius && !discard_keep(cam, X2, rw, bt, a.g2, l)) continue;
+      if (a.radius && !discard_keep(cam, zd, rw, bt, a.g2, l)) continue;
       if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
       unsigned long long* slot = cam.key[l] + (int64_t)pv * (cam.w >> l) + pu;
       if (key < __ldcg(slot)) atomicMin(slot, key);
@@ -96,17 +95,17 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t mask = 0;  // bit l: the point is in Lambda of its layer-l pixel
-    float X0, X1, X2, u0, v0;
+    float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd;
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-    if ((X2 > a.znear) && !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
-      camera(cam, X0, X1, X2, u0, v0);
+    if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) &&
+        !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
       const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
       int64_t pix[kL];
       uint32_t zb[kL];
 #pragma unroll
       for (int l = 0; l < kL; ++l) {
         int32_t pu, pv;
-        const bool keep = l < a.levels && (!a.radius || discard_keep(cam, X2, rw, bt, a.g2, l));
+        const bool keep = l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
         pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? (int64_t)pv * (cam.w >> l) + pu : -1;
       }
 #pragma unroll
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
       bool loaded = false;
 #pragma unroll
       for (int l = 0; l < kL; ++l) {
-        if (pix[l] < 0 || !(X2 <= __fmul_rn(__uint_as_float(zb[l]), a.a1))) continue;
+        if (pix[l] < 0 || !(zd <= __fmul_rn(__uint_as_float(zb[l]), a.a1))) continue;
         if (!loaded) {
           load_desc<C, TF>(feat, i, a.log_desc, f);
           loaded = true;

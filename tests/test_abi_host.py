@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def _structs(adop, n=10, c=4, levels=4, w=64, h=48, flags=0):
     from paper_2110_06635_gb300 import _abi as A
     pts = A.adop_points(n, c, A.ADOP_F32, 0x10000, 0x20000, None)
-    K = A.adop_intrinsics(w, h, 50.0, 50.0, w / 2, h / 2, 0, 0, 0, 0, 0)
+    K = A.adop_intrinsics(w, h, 50.0, 50.0, w / 2, h / 2, 0, 0, 0, 0, 0, 0)
     R = (ct.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
     T = A.adop_pose(R, (ct.c_float * 3)(0, 0, 2))
     cam = (A.adop_camera * 1)(A.adop_camera(K, T, A.adop_photometric()))

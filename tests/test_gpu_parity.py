@@ -180,3 +180,19 @@ def test_log_descriptors(adop, orc, tiny, dtype):
         g = gpu_run(adop, sc, cams, dtype, grads=G, flags=adop.ADOP_FLAG_LOG_DESCRIPTORS, vis=vis)
         r = oracle_run(orc, sc, cams, dtype, grads=G, log_desc=True)
         compare(g, r, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_fisheye_camera(adop, orc, dtype):
+    """The fisheye model (stereographic, distance as depth) close to the
+    spheres, with points far off axis and some behind the image plane."""
+    from scipy.spatial.transform import Rotation
+    sc = scenes.tiny_spheres(12000, 4, seed=81)
+    R = Rotation.from_rotvec([0.05, -0.1, 0.02]).as_matrix().astype(np.float32)
+    cam = scenes.Camera(160, 120, 48.0, 48.0, 80.5, 60.5, k1=0.05, k2=-0.02, k3=0.004, R=R,
+                        t=np.array([-0.45, -0.35, 0.6], np.float32), model=1)
+    G = _grads([cam], 4, 4, 21)
+    g = gpu_run(adop, sc, [cam], dtype, grads=G)
+    r = oracle_run(orc, sc, [cam], dtype, grads=G)
+    compare(g, r, dtype)
+    assert (g["cnt"][0] > 0).sum() > 1000
