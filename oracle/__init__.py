@@ -63,7 +63,11 @@ def _load():
         lib.orc_pyramid_pixels.argtypes = [ct.c_int32, ct.c_int32, ct.c_int]
         lib.orc_pyramid_pixels.restype = ct.c_int64
         lib.orc_forward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P, ct.c_int32, ct.c_float,
-                                    ct.c_float, _P, _P, _P, ct.c_float, ct.c_int32, _P, _P, _P, _P, _P]
+                                    ct.c_float, _P, _P, _P, ct.c_float, ct.c_int32, _P, ct.c_int32, ct.c_int32,
+                                    _P, _P, _P, _P, _P]
+        lib.orc_camera_inverse_f64.argtypes = [_P, ct.c_double, ct.c_double, _P]
+        lib.orc_env_sample.argtypes = [_P, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P, _P]
+        lib.orc_env_grad.argtypes = [_P, _P, ct.c_int32, ct.c_int32, _P, _P, ct.c_int32, ct.c_int32, _P]
         lib.orc_knn_radius.argtypes = [ct.c_int64, _P, ct.c_int32, _P]
         lib.orc_forward.restype = ct.c_int
         lib.orc_project_jac_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
@@ -214,7 +218,7 @@ def knn_radius(xyz, k: int = 4) -> np.ndarray:
 
 
 def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None,
-            radius=None, beta=None, gamma=1.5, log_desc=False) -> Forward:
+            radius=None, beta=None, gamma=1.5, log_desc=False, env=None) -> Forward:
     """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend);
     with radius/beta, stochastic point discarding (Eq. discard) at every layer."""
     lib = _load()
@@ -233,12 +237,45 @@ def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, n
     rad = None if radius is None else np.ascontiguousarray(radius, dtype=np.float32)
     bet = None if radius is None else np.ascontiguousarray(beta, dtype=np.float32)
     K, T = _intr(cam), _pose(cam)
+    E = None if env is None else np.ascontiguousarray(env, dtype=np.float64)
+    eh, ew = (0, 0) if env is None else E.shape[1:]
     rc = lib.orc_forward(n, _ptr(xyz), c, _ptr(f64), _ptr(nrm), ct.byref(K), ct.byref(T), int(levels),
                          ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(rad), _ptr(bet), ct.c_float(gamma),
-                         int(bool(log_desc)), _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
+                         int(bool(log_desc)), _ptr(E), ew, eh, _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
     if rc != 0:
         raise MemoryError("oracle forward: allocation failed")
     return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)
+
+
+def camera_inverse(cam, u0, v0):
+    """Unit camera-space direction of the ray through layer-0 coordinates (u0, v0)."""
+    lib = _load()
+    d = np.zeros(3)
+    K = _intr(cam)
+    lib.orc_camera_inverse_f64(ct.byref(K), float(u0), float(v0), _ptr(d))
+    return d
+
+
+def env_sample(env, direction):
+    """Bilinear equirectangular lookup of a world direction in env (c x h x w)."""
+    lib = _load()
+    E = np.ascontiguousarray(env, dtype=np.float64)
+    c, eh, ew = E.shape
+    out = np.zeros(c)
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    lib.orc_env_sample(_ptr(E), c, ew, eh, _ptr(d), _ptr(out), None, None)
+    return out
+
+
+def env_grad(fwd, cam, G, env_shape):
+    """dL/dE of the environment map (c x h x w) from the forward's empty pixels."""
+    lib = _load()
+    c, eh, ew = env_shape
+    dE = np.zeros((c, eh, ew))
+    K, T = _intr(cam), _pose(cam)
+    Gv = np.ascontiguousarray(G, dtype=np.float64)
+    lib.orc_env_grad(ct.byref(K), ct.byref(T), fwd.levels, c, _ptr(fwd.cnt), _ptr(Gv), ew, eh, _ptr(dE))
+    return dE
 
 
 @dataclass

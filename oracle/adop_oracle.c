@@ -221,16 +221,134 @@ static void project_all(int64_t n, const float* xyz, const float* normals,
 }
 
 /* ------------------------------------------------------------------ */
+/* Environment map (Sec. 3.1, "Environment Map"; Eq. blend, empty pixels) */
+/* ------------------------------------------------------------------ */
+
+/* Inverse camera model C^-1 in FP64: the unit camera-space direction of the
+ * ray through layer-0 pixel coordinates (u0, v0).  Pinhole: the distortion is
+ * inverted by fixed-point iteration (xn, yn) = ((xd, yd) - tangential) / d(r2)
+ * until it no longer moves; fisheye: the radial polynomial r d(r^2) = r_d is
+ * inverted by Newton's method, then the stereographic projection. */
+void orc_camera_inverse_f64(const orc_intrinsics* K, double u0, double v0, double* dir) {
+    const double xd = (u0 - K->cx) / K->fx, yd = (v0 - K->cy) / K->fy;
+    const double k1 = K->k1, k2 = K->k2, k3 = K->k3, p1 = K->p1, p2 = K->p2;
+    if (K->model == 1) {
+        const double rd = sqrt(xd * xd + yd * yd);
+        double r = rd;
+        for (int it = 0; it < 100; ++it) {
+            const double r2 = r * r;
+            const double f = r * (1.0 + k1 * r2 + k2 * r2 * r2 + k3 * r2 * r2 * r2) - rd;
+            const double fp = 1.0 + 3.0 * k1 * r2 + 5.0 * k2 * r2 * r2 + 7.0 * k3 * r2 * r2 * r2;
+            const double step = f / fp;
+            r -= step;
+            if (fabs(step) <= 1e-15 * (1.0 + r)) break;
+        }
+        const double xn = rd > 0.0 ? xd * r / rd : 0.0, yn = rd > 0.0 ? yd * r / rd : 0.0;
+        const double r2 = xn * xn + yn * yn;
+        dir[0] = 4.0 * xn / (4.0 + r2);
+        dir[1] = 4.0 * yn / (4.0 + r2);
+        dir[2] = (4.0 - r2) / (4.0 + r2);
+        return;
+    }
+    double xn = xd, yn = yd;
+    for (int it = 0; it < 500; ++it) {
+        const double r2 = xn * xn + yn * yn;
+        const double d = 1.0 + k1 * r2 + k2 * r2 * r2 + k3 * r2 * r2 * r2;
+        const double tx = 2.0 * p1 * xn * yn + p2 * (r2 + 2.0 * xn * xn);
+        const double ty = p1 * (r2 + 2.0 * yn * yn) + 2.0 * p2 * xn * yn;
+        const double nx = (xd - tx) / d, ny = (yd - ty) / d;
+        const double moved = fabs(nx - xn) + fabs(ny - yn);
+        xn = nx;
+        yn = ny;
+        if (moved <= 1e-16) break;
+    }
+    const double nrm = sqrt(xn * xn + yn * yn + 1.0);
+    dir[0] = xn / nrm;
+    dir[1] = yn / nrm;
+    dir[2] = 1.0 / nrm;
+}
+
+/* Equirectangular lookup of a world direction in E (c x eh x ew): longitude
+ * phi = atan2(dx, dz), colatitude theta = acos(dy); texel coordinates
+ * (phi + pi) / (2 pi) ew - 1/2 and theta / pi eh - 1/2 (texel centres at
+ * integers); bilinear, wrapping in longitude, clamped in colatitude.
+ * out (c values, may be NULL) receives the sample; tex[4] and wts[4] (may be
+ * NULL) the texels and weights used. */
+void orc_env_sample(const double* env, int32_t c, int32_t ew, int32_t eh, const double* d, double* out,
+                    int64_t* tex, double* wts) {
+    const double pi = 3.14159265358979323846;
+    const double phi = atan2(d[0], d[2]);
+    const double dy = d[1] < -1.0 ? -1.0 : (d[1] > 1.0 ? 1.0 : d[1]);
+    const double theta = acos(dy);
+    const double ue = (phi + pi) / (2.0 * pi) * ew - 0.5;
+    const double ve = theta / pi * eh - 0.5;
+    const double fu0 = floor(ue), fv0 = floor(ve);
+    const double fu = ue - fu0, fv = ve - fv0;
+    int64_t iu0 = (int64_t)fu0, iv0 = (int64_t)fv0;
+    int64_t iu[2] = {((iu0 % ew) + ew) % ew, (((iu0 + 1) % ew) + ew) % ew};
+    int64_t iv[2] = {iv0 < 0 ? 0 : (iv0 >= eh ? eh - 1 : iv0), iv0 + 1 < 0 ? 0 : (iv0 + 1 >= eh ? eh - 1 : iv0 + 1)};
+    const double w[4] = {(1 - fu) * (1 - fv), fu * (1 - fv), (1 - fu) * fv, fu * fv};
+    const int64_t t[4] = {iv[0] * ew + iu[0], iv[0] * ew + iu[1], iv[1] * ew + iu[0], iv[1] * ew + iu[1]};
+    for (int ch = 0; out && ch < c; ++ch) {
+        double v = 0.0;
+        for (int k = 0; k < 4; ++k) v += w[k] * env[(int64_t)ch * ew * eh + t[k]];
+        out[ch] = v;
+    }
+    if (tex)
+        for (int k = 0; k < 4; ++k) {
+            tex[k] = t[k];
+            wts[k] = w[k];
+        }
+}
+
+/* World direction of the ray through pixel (pu, pv) of layer l: C^-1 at the
+ * layer-0 coordinates (pu 2^l, pv 2^l) of the pixel's centre, then R^T. */
+static void pixel_ray(const orc_intrinsics* K, const orc_pose* T, int l, int32_t pu, int32_t pv, double* dw) {
+    double dc[3];
+    orc_camera_inverse_f64(K, ldexp((double)pu, l), ldexp((double)pv, l), dc);
+    for (int k = 0; k < 3; ++k)
+        dw[k] = (double)T->R[0 * 3 + k] * dc[0] + (double)T->R[1 * 3 + k] * dc[1] + (double)T->R[2 * 3 + k] * dc[2];
+}
+
+/* dL/dE of the environment map: every empty pixel of every layer adds its
+ * upstream gradient G (c x h_l x w_l planar, concatenated) to the texels it
+ * sampled, with the bilinear weights.  dE (c x eh x ew) is overwritten. */
+void orc_env_grad(const orc_intrinsics* K, const orc_pose* T, int32_t levels, int32_t c, const uint32_t* cnt,
+                  const double* G, int32_t ew, int32_t eh, double* dE) {
+    for (int64_t j = 0; j < (int64_t)c * ew * eh; ++j) dE[j] = 0.0;
+    for (int l = 0; l < levels; ++l) {
+        const int64_t off = layer_offset(K->w, K->h, l);
+        const int32_t wl = K->w >> l, hl = K->h >> l;
+        const int64_t np = (int64_t)wl * hl;
+        for (int32_t pv = 0; pv < hl; ++pv)
+            for (int32_t pu = 0; pu < wl; ++pu) {
+                const int64_t p = (int64_t)pv * wl + pu;
+                if (cnt[off + p] != 0) continue;
+                double dw[3];
+                int64_t tex[4];
+                double wts[4];
+                pixel_ray(K, T, l, pu, pv, dw);
+                orc_env_sample(NULL, c, ew, eh, dw, NULL, tex, wts); /* texels and weights only */
+                for (int ch = 0; ch < c; ++ch)
+                    for (int k = 0; k < 4; ++k)
+                        dE[(int64_t)ch * ew * eh + tex[k]] += wts[k] * G[c * off + (int64_t)ch * np + p];
+            }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Forward (Eq. render, Eq. depthtest, Eq. blend)                       */
 /* ------------------------------------------------------------------ */
 
 /*
  * orc_forward: one camera.
  *   feat       n x c, double
- *   background c doubles or NULL (= 0): the value of an empty pixel.  The
- *              paper samples an environment map there; a constant stands in.
+ *   background c doubles or NULL (= 0): the value of an empty pixel when no
+ *              environment map is given.
  *   radius, beta, gamma  stochastic discarding (Eq. discard): per-point world
  *              radius and uniform draw in [0,1); radius NULL = no discarding.
+ *   env        environment map (c x env_h x env_w, FP64) sampled for empty
+ *              pixels instead of the background; NULL = background.
  * Outputs (all over the concatenated pyramid of `levels` layers):
  *   keys  uint64 per pixel; cnt  |Lambda| per pixel; img  c x h_l x w_l;
  *   pix   n x levels pixel id or -1 (may be NULL); zf  n depths (may be NULL).
@@ -240,6 +358,7 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
                 const orc_intrinsics* K, const orc_pose* T, int32_t levels, float alpha,
                 float znear, const double* background,
                 const float* radius, const float* beta, float gamma, int32_t log_desc,
+                const double* env, int32_t env_w, int32_t env_h,
                 uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out) {
     int64_t npx = orc_pyramid_pixels(K->w, K->h, levels);
     /* Logarithmic descriptors (Sec. 3.2) are converted to linear values before
@@ -291,21 +410,31 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
         }
     }
 
-    /* Step 5: Eq. blend -- the mean over Lambda, or the background. */
+    /* Step 5: Eq. blend -- the mean over Lambda, or, for an empty pixel, the
+     * environment map E(R^T C^-1(u, v)) (or the constant background). */
+    double* ev = (double*)malloc(sizeof(double) * (size_t)(c + 1));
+    if (!ev) return -1;
     for (int l = 0; l < levels; ++l) {
         int64_t off = layer_offset(K->w, K->h, l);
-        int64_t np = (int64_t)(K->w >> l) * (K->h >> l);
+        const int32_t wl = K->w >> l;
+        int64_t np = (int64_t)wl * (K->h >> l);
         for (int64_t p = 0; p < np; ++p) {
+            if (cnt[off + p] == 0 && env) {
+                double dw[3];
+                pixel_ray(K, T, l, (int32_t)(p % wl), (int32_t)(p / wl), dw);
+                orc_env_sample(env, c, env_w, env_h, dw, ev, NULL, NULL);
+            }
             for (int ch = 0; ch < c; ++ch) {
                 double v;
                 if (cnt[off + p] == 0)
-                    v = background ? background[ch] : 0.0;
+                    v = env ? ev[ch] : (background ? background[ch] : 0.0);
                 else
                     v = sum[(off + p) * c + ch] / (double)cnt[off + p];
                 img[c * off + (int64_t)ch * np + p] = v;
             }
         }
     }
+    free(ev);
     free(sum);
     free(lin);
     if (!pix_out) free(pix);

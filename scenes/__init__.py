@@ -243,6 +243,24 @@ def crf_gamma_lut(n: int = 256, gamma: float = 0.45) -> np.ndarray:
     return np.stack([x ** gamma] * 3).astype(np.float32)
 
 
+def env_map(c: int, eh: int = 64, ew: int = 128, seed: int = 1006, noise: float = 0.05) -> np.ndarray:
+    """A c x eh x ew FP32 equirectangular environment map: a few random
+    low-frequency waves in longitude and colatitude (sky-like, smooth across
+    the seam) plus a little per-texel noise, values around [0, 1]."""
+    rng = np.random.default_rng(seed)
+    phi = (np.arange(ew) + 0.5) / ew * 2 * np.pi - np.pi
+    theta = (np.arange(eh) + 0.5) / eh * np.pi
+    P, T = np.meshgrid(phi, theta)
+    out = np.empty((c, eh, ew), np.float64)
+    for ch in range(c):
+        v = np.full_like(P, 0.5)
+        for _ in range(4):
+            a, b = rng.integers(1, 4), rng.integers(1, 4)
+            v += rng.uniform(-0.15, 0.15) * np.cos(a * P + rng.uniform(0, 2 * np.pi)) * np.cos(b * T)
+        out[ch] = v + noise * rng.standard_normal(P.shape)
+    return out.astype(np.float32)
+
+
 def tiny_camera() -> Camera:
     """256^2, fx = fy = 205, principal point at the centre, k1 = 0.01; at
     (0,0,-2) looking at the origin (R = I, t = (0,0,2))."""
