@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--profile-only", action="store_true", help="a few steps, no extras (for ncu)")
     ap.add_argument("--no-train", action="store_true", help="skip the 16-camera training step")
     ap.add_argument("--no-discard", action="store_true", help="skip the stochastic-discarding variant")
+    ap.add_argument("--no-env", action="store_true", help="skip the environment-map variant")
     ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -238,7 +239,8 @@ def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: 
 
 
 class Workload:
-    def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None, discard: bool = False):
+    def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None, discard: bool = False,
+                 env: bool = False):
         import torch
         import paper_2110_06635_gb300 as adop
         import scenes
@@ -270,7 +272,12 @@ class Workload:
             self.beta = torch.rand(scene.n, generator=g, device=device)
             flags |= adop.ADOP_FLAG_DISCARD
         self.pts = adop.Points(self.xyz, self.feat, None, self.radius, self.beta)
-        self.params = adop.Params(LEVELS, 0.01, 1e-3, None, flags, 1.5)
+        self.env = self.genv = None
+        if env:
+            # the paper's 1024^2 spherical map of neural features, read as equirectangular
+            self.env = torch.from_numpy(scenes.env_map(self.c, 1024, 1024, seed=2025)).to(device)
+            self.genv = torch.zeros_like(self.env)
+        self.params = adop.Params(LEVELS, 0.01, 1e-3, None, flags, 1.5, self.env)
         self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device, self.n)
         self.ws = adop.alloc_workspace(self.pts, [cam], self.params, None, device)
         G = scenes.upstream_grad(cam.w, cam.h, LEVELS, self.c, 2024)
@@ -310,6 +317,11 @@ class Workload:
                                             stream_ptr)
         if st != 0:
             raise RuntimeError(self._lib.adop_last_error().decode())
+        if self.env is not None:
+            st = self._lib.adop_env_backward(self._cams, 1, ct.byref(self._pr), self.c, self._fr, self._g,
+                                             self.genv.data_ptr(), stream_ptr)
+            if st != 0:
+                raise RuntimeError(self._lib.adop_last_error().decode())
 
 
 def run_ours(args, dist, rank, world):
@@ -379,6 +391,33 @@ def bench_discard(device, steps: int, warmup: int, flush) -> dict:
            "ms_per_step": round(total_ms / steps, 4),
            "points_in_lambda_per_layer": kept,
            "radius_preprocess_ms": round(wl.radius_ms, 2),
+           "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
+    del wl
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_env(device, steps: int, warmup: int, flush) -> dict:
+    """The headline workload with an environment map (Sec. 3.1): a 1024 x 1024
+    equirectangular map of C = 8 FP32 features sampled for the empty pixels,
+    and its gradient (adop_env_backward) in every step."""
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+    wl = Workload(5_000_000, "bf16", device, env=True)
+    sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(warmup):
+        wl.step(sp)
+    torch.cuda.synchronize()
+    empty = float((wl.frame.count == 0).float().mean().item())
+    adop.adop_profile_enable(True)
+    adop.adop_profile_collect()
+    total_ms, _ = timed_steps(lambda: wl.step(sp), steps, flush, None, device)
+    ks = adop.adop_profile_collect()
+    adop.adop_profile_enable(False)
+    out = {"workload": "the headline view with a 1024x1024 C=8 environment map and its gradient",
+           "value": round(wl.n * steps / (total_ms / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(total_ms / steps, 4), "empty_pixel_fraction": round(empty, 4),
            "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
     del wl
     torch.cuda.empty_cache()
@@ -690,6 +729,10 @@ def main():
         if not args.no_discard:
             fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
             line["stochastic_discard"] = bench_discard(device, args.steps, args.warmup, lambda: fb.zero_())
+            del fb
+        if not args.no_env:
+            fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+            line["environment_map"] = bench_env(device, args.steps, args.warmup, lambda: fb.zero_())
             del fb
         if not args.no_train:
             line["training_step"] = bench_training_step(device)

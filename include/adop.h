@@ -33,7 +33,7 @@ extern "C" {
 
 #define ADOP_MAX_LEVELS 8          /* pyramid layers per camera (the paper uses 4) */
 #define ADOP_MAX_CAMERAS 64        /* cameras per call */
-#define ADOP_ABI_VERSION 1
+#define ADOP_ABI_VERSION 2
 
 struct CUstream_st;
 typedef struct CUstream_st* adop_stream; /* == cudaStream_t */
@@ -130,7 +130,21 @@ typedef struct {
 /* levels: pyramid layers L (1..ADOP_MAX_LEVELS); alpha: fuzzy depth-test
  * threshold of Eq. depthtest (the paper uses 0.01); znear: points with
  * depth z <= znear are discarded; background: c FP32 values (device) shown
- * where no point lands (the paper's environment map), NULL = zeros.
+ * where no point lands when there is no environment map, NULL = zeros.
+ * env (Sec. 3.1, environment map; NULL = none): c x env_h x env_w FP32
+ * planar (device), an equirectangular map of world directions.  A pixel
+ * where no point lands shows E(R^T C^-1(u0, v0)) instead of the background:
+ * the ray through the pixel centre (layer-l pixel (p, q) at layer-0
+ * coordinates (p 2^l, q 2^l)), C^-1 the inverse camera model (pinhole:
+ * fixed-point inversion of the distortion; fisheye: Newton on the radial
+ * polynomial, then the inverse stereographic map), looked up at longitude
+ * phi = atan2(d_x, d_z), colatitude theta = acos(d_y), texel coordinates
+ * ((phi + pi) / (2 pi) env_w - 1/2, theta / pi env_h - 1/2), bilinear,
+ * wrapping in longitude and clamped in colatitude (FP32).  The empty-target
+ * case of the spatial gradient then uses that value; the pose gets no
+ * gradient through the lookup.  env_w, env_h in [1, 16384].  A pixel beyond
+ * the fold of a non-monotone radial polynomial has no ray; it still samples
+ * in-range texels, but which ones is unspecified.
  * gamma (> 0, the paper uses 1.5): with ADOP_FLAG_DISCARD a point is
  * rendered at layer l only if r_screen / sqrt(1 - beta) > 1 / gamma, where
  * r_screen = fx r_world / (z 2^l); evaluated in FP32 as
@@ -144,6 +158,8 @@ typedef struct {
     const float* background;
     uint32_t flags;
     float gamma;
+    const float* env;
+    int32_t env_w, env_h;
 } adop_params;
 
 /* Per-camera frame.  image[l]: output, c x h_l x w_l planar in out_dtype
@@ -281,6 +297,8 @@ typedef struct {
     uint32_t flags;            /* ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL */
     adop_dtype out_dtype;      /* output image type */
     const float* background;   /* c FP32 (device) or NULL */
+    const float* env;          /* environment map as in adop_params, or NULL */
+    int32_t env_w, env_h;
 } adop_serve_config;
 
 typedef struct {
@@ -324,6 +342,21 @@ adop_status adop_serve_destroy(adop_server* s);
  *               (no entries for a camera without a LUT); NULL = not computed
  * crf_n <= 4000.  Workspace: adop_photometric_workspace_bytes(n_cam).
  */
+/*
+ * Gradient of the environment map (Sec. 3.1), accumulated (+=) into
+ * grad_env (c x env_h x env_w FP32, device): every pixel of every layer where
+ * no point landed adds its upstream gradient to the four texels it sampled,
+ * with the bilinear weights.  grad_image[k * levels + l] as in
+ * adop_render_backward (at layer 0 it is chained through the photometric
+ * epilogue when that is on); frames must carry the forward's count[l] of
+ * every layer.  params->env must be the map the forward sampled.  Needs no
+ * workspace.  Texel sums use FP32 atomics: their order, and so the last bits,
+ * vary between runs.
+ */
+adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam, const adop_params* params, int32_t c,
+                              const adop_frame* frames, const float* const* grad_image, float* grad_env,
+                              adop_stream stream);
+
 size_t adop_photometric_workspace_bytes(int32_t n_cam);
 adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, const adop_params* params,
                                       int32_t c, const adop_frame* frames, const float* const* grad_image0,

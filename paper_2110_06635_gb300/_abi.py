@@ -60,7 +60,8 @@ class adop_points(ct.Structure):
 
 class adop_params(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float), ("background", ct.c_void_p),
-                ("flags", ct.c_uint32), ("gamma", ct.c_float)]
+                ("flags", ct.c_uint32), ("gamma", ct.c_float), ("env", ct.c_void_p), ("env_w", ct.c_int32),
+                ("env_h", ct.c_int32)]
 
 
 class adop_frame(ct.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "adop_render_backward_noalloc": (ct.c_int, [_P, _P, ct.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "adop_point_radius_workspace_bytes": (ct.c_size_t, [ct.c_int64]),
     "adop_point_radius": (ct.c_int, [_P, ct.c_int64, ct.c_int32, _P, _P, ct.c_size_t, _P]),
+    "adop_env_backward": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32, _P, _P, _P, _P]),
     "adop_photometric_workspace_bytes": (ct.c_size_t, [ct.c_int32]),
     "adop_photometric_backward": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32, _P, _P, _P, _P, _P, ct.c_size_t, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
@@ -170,9 +172,12 @@ class Params:
     background: object = None  # c float32 CUDA tensor or None
     flags: int = 0
     gamma: float = 1.5         # stochastic discarding (with ADOP_FLAG_DISCARD)
+    env: object = None         # c x env_h x env_w float32 CUDA tensor (environment map) or None
 
     def struct(self) -> adop_params:
-        return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags, self.gamma)
+        eh, ew = (0, 0) if self.env is None else (int(self.env.shape[-2]), int(self.env.shape[-1]))
+        return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags, self.gamma,
+                           _dev_ptr(self.env), ew, eh)
 
 
 def camera_struct(cam, crf_lut=None) -> adop_camera:
@@ -342,6 +347,21 @@ def adop_photometric_backward(cams, params: Params, c: int, frames, grad_image0,
                                          _dev_ptr(grad_crf), wp, wn, _stream_ptr(stream)))
 
 
+def adop_env_backward(cams, params: Params, c: int, frames, grad_images, grad_env, stream=None, crf_luts=None):
+    """Gradient of the environment map params.env (Sec. 3.1), accumulated into
+    grad_env (same shape) from grad_images[k][l] (dL/dI of camera k, layer l)
+    at the pixels where no point landed."""
+    lib = load()
+    pr = params.struct()
+    arr = _cams_array(cams, crf_luts)
+    fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
+    L = params.levels
+    gi = (ct.c_void_p * (len(cams) * L))(*[_dev_ptr(g[l] if g is not None else None)
+                                          for g in grad_images for l in range(L)])
+    _check(lib.adop_env_backward(arr, len(cams), ct.byref(pr), int(c), fr, gi, _dev_ptr(grad_env),
+                                 _stream_ptr(stream)))
+
+
 def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):
     """Forward pass (Sec. 3.1) of every camera; fills each frame's images and state."""
     lib = load()
@@ -402,7 +422,8 @@ def adop_render_backward_noalloc(points: Points, cams, params: Params, frames, g
 class adop_serve_config(ct.Structure):
     _fields_ = [("mem_budget_bytes", ct.c_size_t), ("max_slots", ct.c_int32), ("streams", ct.c_int32),
                 ("max_batch", ct.c_int32), ("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float),
-                ("flags", ct.c_uint32), ("out_dtype", ct.c_int32), ("background", ct.c_void_p)]
+                ("flags", ct.c_uint32), ("out_dtype", ct.c_int32), ("background", ct.c_void_p),
+                ("env", ct.c_void_p), ("env_w", ct.c_int32), ("env_h", ct.c_int32)]
 
 
 class adop_serve_stats(ct.Structure):
@@ -443,7 +464,7 @@ class Server:
 
     def __init__(self, mem_budget_bytes: int, max_slots: int = 64, streams: int = 4, max_batch: int = 8,
                  levels: int = 4, alpha: float = 0.01, znear: float = 1e-3, flags: int = 0, out_dtype=None,
-                 background=None):
+                 background=None, env=None):
         torch = _torch()
         self.lib = load()
         self.levels = levels
@@ -451,8 +472,10 @@ class Server:
         self._keep = {}
         self._clouds = []
         self._bg = background
+        self._env = env
+        eh, ew = (0, 0) if env is None else (int(env.shape[-2]), int(env.shape[-1]))
         cfg = adop_serve_config(mem_budget_bytes, max_slots, streams, max_batch, levels, alpha, znear, flags,
-                                dtype_code(self.out_dtype), _dev_ptr(background))
+                                dtype_code(self.out_dtype), _dev_ptr(background), _dev_ptr(env), ew, eh)
         h = ct.c_void_p()
         _check(self.lib.adop_serve_create(ct.byref(cfg), ct.byref(h)))
         self.h = h

@@ -12,7 +12,9 @@ camera's image pyramid and makes it differentiable with respect to
   gradient is that of the left increment at exp(xi) (R, t), which equals
   dL/dxi exactly at xi = 0,
 * ``intrinsics`` (n_cam x 6: fx, fy, cx, cy, k1, k2), replacing the cameras'
-  values.
+  values,
+* ``env`` (c x env_h x env_w float32, the environment map that pixels where
+  no point lands show, Sec. 3.1); its gradient needs ``keep_state=True``.
 
 ``keep_state=True`` keeps each camera's per-pixel key/count/sum buffers and
 per-point layer mask for the backward pass; ``keep_state=False`` keeps only
@@ -84,7 +86,7 @@ def _effective_cameras(cameras, xi, intrinsics):
 
 class _Rasterize(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, xyz, feat, xi, intr, cams, params, out_dtype, keep_state, crf_luts, discard):
+    def forward(ctx, xyz, feat, xi, intr, env, cams, params, out_dtype, keep_state, crf_luts, discard):
         dev = xyz.device
         levels = params.levels
         pts = A.Points(xyz.contiguous(), feat.contiguous(), None, *discard)
@@ -122,26 +124,35 @@ class _Rasterize(torch.autograd.Function):
         gpose = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
         gintr = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
         params = A.Params(ctx.params.levels, ctx.params.alpha, ctx.params.znear, ctx.params.background,
-                          ctx.params.flags | A.ADOP_FLAG_GRAD_ASSIGN, ctx.params.gamma)
+                          ctx.params.flags | A.ADOP_FLAG_GRAD_ASSIGN, ctx.params.gamma, ctx.params.env)
         pts = A.Points(xyz.contiguous(), feat.contiguous(), None, *ctx.discard)
         A.adop_render_backward(pts, ctx.cams, params, ctx.frames, gimgs, gfeat, gxyz, gpose, gintr, ctx.ws,
                                crf_luts=ctx.crf_luts)
+        g_env = None
+        if ctx.needs_input_grad[4]:
+            g_env = torch.zeros_like(ctx.params.env, dtype=torch.float32)
+            A.adop_env_backward(ctx.cams, params, c, ctx.frames, gimgs, g_env, crf_luts=ctx.crf_luts)
         g_feat = None if gfeat is None else gfeat.to(feat.dtype)
         g_xi = None if not ctx.needs_input_grad[2] else gpose.to(ctx.xi_dev)
         g_intr = None if not ctx.needs_input_grad[3] else gintr.to(ctx.intr_dev)
-        return gxyz, g_feat, g_xi, g_intr, None, None, None, None, None, None
+        return gxyz, g_feat, g_xi, g_intr, g_env, None, None, None, None, None, None
 
 
 def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01, znear=1e-3, background=None,
-              flags=0, out_dtype=torch.float32, keep_state=True, crf_luts=None, radius=None, beta=None, gamma=1.5):
+              flags=0, out_dtype=torch.float32, keep_state=True, crf_luts=None, radius=None, beta=None, gamma=1.5,
+              env=None):
     """Differentiable render of every camera; returns [camera][layer] images
     (c x h_l x w_l).  See the module docstring for the gradients.  With
     radius and beta (float32 per point), stochastic point discarding
-    (Eq. discard) with threshold gamma."""
+    (Eq. discard) with threshold gamma; with env (c x env_h x env_w float32),
+    empty pixels sample the environment map."""
     cams = _effective_cameras(cameras, xi, intrinsics)
     if radius is not None:
         flags |= A.ADOP_FLAG_DISCARD
-    params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN, gamma)
-    outs = _Rasterize.apply(xyz, feat, xi, intrinsics, cams, params, out_dtype, keep_state, crf_luts,
+    if env is not None and env.requires_grad and not keep_state:
+        raise ValueError("the environment map's gradient needs keep_state=True (the forward's per-pixel counts)")
+    env_data = None if env is None else env.detach().contiguous()
+    params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN, gamma, env_data)
+    outs = _Rasterize.apply(xyz, feat, xi, intrinsics, env, cams, params, out_dtype, keep_state, crf_luts,
                             (radius, beta))
     return [list(outs[k * levels:(k + 1) * levels]) for k in range(len(cameras))]

@@ -347,4 +347,102 @@ __device__ __forceinline__ float epilogue(const DevCam& cam, int ch, int32_t u, 
   return y;
 }
 
+// ---------------------------------------------------------------------------
+// environment map (Sec. 3.1): the value of a pixel where no point lands
+// ---------------------------------------------------------------------------
+
+constexpr int kInvertSteps = 20;  // fixed-point / Newton steps of the inverse camera
+
+// Inverse camera model C^-1: the unit camera-space direction of the ray
+// through layer-0 pixel coordinates (u0, v0).  Pinhole: the Brown-Conrady
+// distortion is undone by fixed-point steps (xn, yn) <- ((xd, yd) -
+// tangential(xn, yn)) / radial(xn, yn), which contract for the moderate
+// distortion of calibrated lenses; fisheye: Newton steps on
+// r radial(r^2) = r_d, then the inverse stereographic map
+// (xn, yn) -> (4 xn, 4 yn, 4 - r^2) / (4 + r^2).  FP32.
+__device__ __forceinline__ void camera_inverse(const DevCam& cam, float u0, float v0, float (&d)[3]) {
+  const float xd = (u0 - cam.cx) / cam.fx, yd = (v0 - cam.cy) / cam.fy;
+  if (cam.model == 1) {
+    const float rd = sqrtf(xd * xd + yd * yd);
+    float r = rd;
+#pragma unroll 4
+    for (int it = 0; it < kInvertSteps; ++it) {
+      const float r2 = r * r;
+      const float f = r * (1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3))) - rd;
+      const float fp = 1.0f + r2 * (3.0f * cam.k1 + r2 * (5.0f * cam.k2 + r2 * 7.0f * cam.k3));
+      r -= f / fp;
+    }
+    const float s = rd > 0.0f ? r / rd : 1.0f;
+    const float xn = xd * s, yn = yd * s;
+    const float r2 = xn * xn + yn * yn;
+    const float inv = 1.0f / (4.0f + r2);
+    d[0] = 4.0f * xn * inv;
+    d[1] = 4.0f * yn * inv;
+    d[2] = (4.0f - r2) * inv;
+    return;
+  }
+  float xn = xd, yn = yd;
+#pragma unroll 4
+  for (int it = 0; it < kInvertSteps; ++it) {
+    const float r2 = xn * xn + yn * yn;
+    const float rad = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
+    const float tx = 2.0f * cam.p1 * xn * yn + cam.p2 * (r2 + 2.0f * xn * xn);
+    const float ty = cam.p1 * (r2 + 2.0f * yn * yn) + 2.0f * cam.p2 * xn * yn;
+    xn = (xd - tx) / rad;
+    yn = (yd - ty) / rad;
+  }
+  const float inv = rsqrtf(xn * xn + yn * yn + 1.0f);
+  d[0] = xn * inv;
+  d[1] = yn * inv;
+  d[2] = inv;
+}
+
+// The four texels (indices into one env_h x env_w plane) and bilinear
+// weights that layer-l pixel (pu, pv) samples: world direction
+// R^T C^-1(pu 2^l, pv 2^l), longitude atan2(d_x, d_z) and colatitude
+// acos(d_y) mapped to texel coordinates with centres at integers; longitude
+// wraps, colatitude clamps.  Every index is in range whatever the inputs.
+struct EnvTaps {
+  int32_t t[4];
+  float w[4];
+};
+
+__device__ __forceinline__ EnvTaps env_taps(const DevCam& cam, int32_t ew, int32_t eh, int l, int32_t pu,
+                                            int32_t pv) {
+  constexpr float kPi = 3.14159265358979323846f;
+  float dc[3];
+  camera_inverse(cam, (float)(pu << l), (float)(pv << l), dc);
+  const float dx = cam.R[0] * dc[0] + cam.R[3] * dc[1] + cam.R[6] * dc[2];
+  const float dy = cam.R[1] * dc[0] + cam.R[4] * dc[1] + cam.R[7] * dc[2];
+  const float dz = cam.R[2] * dc[0] + cam.R[5] * dc[1] + cam.R[8] * dc[2];
+  const float phi = atan2f(dx, dz);
+  const float theta = acosf(fminf(fmaxf(dy, -1.0f), 1.0f));
+  const float ue = (phi + kPi) * ((float)ew * (0.5f / kPi)) - 0.5f;
+  const float ve = theta * ((float)eh / kPi) - 0.5f;
+  const float fu0 = floorf(ue), fv0 = floorf(ve);
+  const float fu = ue - fu0, fv = ve - fv0;
+  const int32_t iu0 = (int32_t)fu0, iv0 = (int32_t)fv0;
+  const int32_t ua = ((iu0 % ew) + ew) % ew;
+  const int32_t ub = ua + 1 == ew ? 0 : ua + 1;
+  const int32_t va = min(max(iv0, 0), eh - 1), vb = min(max(iv0 + 1, 0), eh - 1);
+  EnvTaps e;
+  e.t[0] = va * ew + ua;
+  e.t[1] = va * ew + ub;
+  e.t[2] = vb * ew + ua;
+  e.t[3] = vb * ew + ub;
+  e.w[0] = (1.0f - fu) * (1.0f - fv);
+  e.w[1] = fu * (1.0f - fv);
+  e.w[2] = (1.0f - fu) * fv;
+  e.w[3] = fu * fv;
+  return e;
+}
+
+// Sampled value of channels [0, n) of env (c planes of ew x eh) at the taps.
+__device__ __forceinline__ float env_channel(const float* __restrict__ env, int64_t plane, const EnvTaps& e,
+                                             int ch) {
+  const float* E = env + ch * plane;
+  return e.w[0] * __ldg(E + e.t[0]) + e.w[1] * __ldg(E + e.t[1]) + e.w[2] * __ldg(E + e.t[2]) +
+         e.w[3] * __ldg(E + e.t[3]);
+}
+
 }  // namespace adop

@@ -64,18 +64,6 @@ int prof_id(const char* name) {
   return (int)g_prof_names.size() - 1;
 }
 
-// Run one launch; when timing is on, bracket it with events on its stream.
-template <class F>
-cudaError_t timed(const char* name, cudaStream_t s, F&& launch) {
-  if (!g_prof_on) return launch();
-  std::lock_guard<std::mutex> lk(g_prof_mu);
-  ProfRec r{prof_id(name), prof_event(), prof_event()};
-  cudaEventRecord(r.a, s);
-  cudaError_t e = launch();
-  cudaEventRecord(r.b, s);
-  g_prof_recs.push_back(r);
-  return e;
-}
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxPartialBlocks = 4096;
@@ -159,6 +147,11 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
       return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_DISCARD needs a finite gamma > 0");
     if (pts->n > 0 && (!pts->radius || !pts->beta))
       return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_DISCARD needs per-point radius and beta");
+  }
+  if (prm->env) {
+    if (!env_size_ok(prm->env_w, prm->env_h))
+      return fail(ADOP_ERR_INVALID_ARG, "environment map %dx%d outside [1, 16384]^2", prm->env_w, prm->env_h);
+    if (((uintptr_t)prm->env & 3) != 0) return fail(ADOP_ERR_INVALID_ARG, "env must be 4-byte aligned");
   }
   if ((prm->flags & ADOP_FLAG_NORMAL_CULL) && pts->n > 0 && !pts->normals)
     return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_NORMAL_CULL needs normals");
@@ -263,6 +256,9 @@ PointArgs point_args(const adop_points* pts, const adop_params* prm, int ncam) {
   a.feat = pts->feat;
   a.normals = (prm->flags & ADOP_FLAG_NORMAL_CULL) ? pts->normals : nullptr;
   a.background = prm->background;
+  a.env = prm->env;
+  a.env_w = prm->env_w;
+  a.env_h = prm->env_h;
   a.radius = (prm->flags & ADOP_FLAG_DISCARD) ? pts->radius : nullptr;
   a.beta = (prm->flags & ADOP_FLAG_DISCARD) ? pts->beta : nullptr;
   a.g2 = prm->gamma * prm->gamma;
@@ -324,6 +320,21 @@ void* g_scratch_ptr[kMaxDevices] = {};
 }  // namespace
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+int prof_begin(const char* name, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return -1;
+  ProfRec r{prof_id(name), prof_event(), prof_event()};
+  cudaEventRecord(r.a, s);
+  g_prof_recs.push_back(r);
+  return (int)g_prof_recs.size() - 1;
+}
+
+void prof_end(int rec, cudaStream_t s) {
+  if (rec < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (rec < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[rec].b, s);
+}
 
 void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_t flags) {
   memset(&d, 0, sizeof(d));

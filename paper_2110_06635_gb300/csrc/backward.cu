@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const unsigned long long key = cam.key[l][p];
     float I[C], G[GS];
     if (n == 0) {
-#pragma unroll
-      for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
+      const int32_t wl = cam.w >> l;
+      empty_value<C>(cam, a, l, (int32_t)(p % wl), (int32_t)(p / wl), I);
     } else {
       const float fn = (float)n;
 #pragma unroll

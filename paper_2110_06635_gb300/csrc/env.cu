@@ -1,0 +1,113 @@
+// Gradient of the environment map (Sec. 3.1).  An empty pixel's value is
+// the bilinear sample sum_j w_j E[t_j] along its ray, so dL/dE[t_j] gains
+// w_j G for every channel.  One thread per pyramid pixel; pixels with a point
+// return at once, the others recompute their taps (the inverse camera and the
+// equirectangular lookup of the forward), chain layer 0 through the
+// photometric epilogue and add to the four texels with FP32 atomics.
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace adop {
+namespace {
+
+template <int C>
+__global__ void __launch_bounds__(kThreads) k_env_grad(const __grid_constant__ LaunchCams cams,
+                                                       const __grid_constant__ PointArgs a, float* grad_env) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int64_t total = cam.off[a.levels];
+  const int64_t plane = (int64_t)a.env_w * a.env_h;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int l = layer_of(cam, a.levels, g);
+    const float* gl = cam.grad[l];
+    const int64_t p = g - cam.off[l];
+    if (gl == nullptr || cam.cnt[l][p] != 0) continue;
+    const int64_t np = cam.off[l + 1] - cam.off[l];
+    const int32_t wl = cam.w >> l;
+    const int32_t pu = (int32_t)(p % wl), pv = (int32_t)(p / wl);
+    const EnvTaps e = env_taps(cam, a.env_w, a.env_h, l, pu, pv);
+    float G[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) G[k] = __ldg(gl + k * np + p);
+    if (l == 0 && cam.epi) {
+#pragma unroll
+      for (int k = 0; k < (C < 3 ? C : 3); ++k) {
+        float d;
+        epilogue(cam, k, pu, pv, env_channel(a.env, plane, e, k), &d);
+        G[k] *= d;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (G[k] == 0.0f) continue;
+      float* dst = grad_env + k * plane;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (e.w[j] != 0.0f) atomicAdd(dst + e.t[j], e.w[j] * G[k]);
+    }
+  }
+}
+
+adop_status fail(adop_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+}  // namespace
+
+cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s) {
+  ADOP_DISPATCH_C(c, k_env_grad<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a, grad_env));
+  return cudaGetLastError();
+}
+
+}  // namespace adop
+
+using namespace adop;
+
+extern "C" adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam, const adop_params* params,
+                                         int32_t c, const adop_frame* frames, const float* const* grad_image,
+                                         float* grad_env, adop_stream stream) {
+  if (!cams || !params || !frames || !grad_env) return fail(ADOP_ERR_INVALID_ARG, "NULL argument");
+  if (!params->env) return fail(ADOP_ERR_INVALID_ARG, "params->env is NULL: no environment map to differentiate");
+  if (!env_size_ok(params->env_w, params->env_h))
+    return fail(ADOP_ERR_INVALID_ARG, "env_w / env_h outside [1, 16384]");
+  if (((uintptr_t)params->env & 3) != 0 || ((uintptr_t)grad_env & 3) != 0)
+    return fail(ADOP_ERR_INVALID_ARG, "env / grad_env must be 4-byte aligned");
+  if (n_cam < 1 || n_cam > ADOP_MAX_CAMERAS) return fail(ADOP_ERR_INVALID_ARG, "n_cam outside [1, 64]");
+  if (!channels_supported(c)) return fail(ADOP_ERR_UNSUPPORTED, "channel count has no kernels");
+  if (params->levels < 1 || params->levels > ADOP_MAX_LEVELS) return fail(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
+  for (int k = 0; k < n_cam; ++k) {
+    const adop_intrinsics& K = cams[k].K;
+    if (K.w < 1 || K.h < 1 || K.w > 16384 || K.h > 16384)
+      return fail(ADOP_ERR_INVALID_ARG, "image size outside [1, 16384]");
+    if ((K.w >> (params->levels - 1)) < 1 || (K.h >> (params->levels - 1)) < 1)
+      return fail(ADOP_ERR_INVALID_ARG, "image too small for the pyramid");
+    if (K.model != 0 && K.model != 1) return fail(ADOP_ERR_INVALID_ARG, "unknown camera model");
+    for (int l = 0; l < params->levels; ++l)
+      if (!frames[k].count[l] || ((uintptr_t)frames[k].count[l] & 3) != 0)
+        return fail(ADOP_ERR_INVALID_ARG, "the environment map gradient needs the forward's count of every layer");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int k0 = 0; k0 < n_cam; k0 += kMaxCamsPerLaunch) {
+    const int nc = (n_cam - k0) < kMaxCamsPerLaunch ? (n_cam - k0) : kMaxCamsPerLaunch;
+    LaunchCams lc;
+    for (int j = 0; j < nc; ++j) {
+      const int k = k0 + j;
+      set_camera_constants(lc.c[j], cams[k], params->levels, params->flags);
+      for (int l = 0; l < params->levels; ++l) {
+        lc.c[j].cnt[l] = frames[k].count[l];
+        lc.c[j].grad[l] = grad_image ? grad_image[(size_t)k * params->levels + l] : nullptr;
+      }
+    }
+    PointArgs a{};
+    a.env = params->env;
+    a.env_w = params->env_w;
+    a.env_h = params->env_h;
+    a.levels = params->levels;
+    a.ncam = nc;
+    const cudaError_t e = timed("env_grad", s, [&] { return launch_env_grad(lc, a, c, grad_env, s); });
+    if (e != cudaSuccess) return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return ADOP_OK;
+}

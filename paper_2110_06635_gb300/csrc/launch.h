@@ -14,6 +14,8 @@ struct PointArgs {
   const void* feat;
   const float* normals;  // non-NULL only when normal culling is on
   const float* background;
+  const float* env;     // environment map (NULL = background): c x env_h x env_w
+  int32_t env_w, env_h;
   const float* radius;  // stochastic discarding (NULL = off): world radius per point
   const float* beta;    // and uniform draw per point
   float g2;             // f32(gamma * gamma)
@@ -55,6 +57,24 @@ cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s);
 
+// Value of an empty layer-l pixel (pu, pv): the environment map's sample
+// along the pixel's ray, else the background (else zero).
+template <int C>
+__device__ __forceinline__ void empty_value(const DevCam& cam, const PointArgs& a, int l, int32_t pu, int32_t pv,
+                                            float (&v)[C]) {
+  if (a.env) {
+    const EnvTaps e = env_taps(cam, a.env_w, a.env_h, l, pu, pv);
+    const int64_t plane = (int64_t)a.env_w * a.env_h;
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = env_channel(a.env, plane, e, k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = a.background ? __ldg(a.background + k) : 0.0f;
+  }
+}
+
+cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s);
+
 // Pixels of a w x h pyramid of `levels` layers (w_l = w >> l, h_l = h >> l);
 // off (if given) receives the first pixel of every layer and the total.
 inline int64_t pyramid_pixels(int32_t w, int32_t h, int levels, int64_t* off) {
@@ -74,6 +94,22 @@ void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_
 
 // Set the calling thread's adop_last_error() message.
 void set_last_error(const char* msg);
+
+// Kernel timing for adop_profile_enable / adop_profile_collect: events on the
+// launch stream around one launch (prof_begin returns -1 when timing is off).
+int prof_begin(const char* name, cudaStream_t s);
+void prof_end(int rec, cudaStream_t s);
+
+template <class F>
+cudaError_t timed(const char* name, cudaStream_t s, F&& launch) {
+  const int rec = prof_begin(name, s);
+  const cudaError_t e = launch();
+  prof_end(rec, s);
+  return e;
+}
+
+// Environment map sizes the lookup accepts (texel indices stay in int32).
+inline bool env_size_ok(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
 
 // Channel counts with compiled kernels.
 inline bool channels_supported(int c) { return c == 1 || c == 2 || c == 3 || c == 4 || c == 8 || c == 16; }

@@ -3,7 +3,8 @@
 // coefficients, and the response-curve LUT.
 //
 // One pass over the layer-0 pixels of every camera: each thread recomputes
-// the pre-epilogue value I = sum / |Lambda| (or the background), the
+// the pre-epilogue value I = sum / |Lambda| (or the environment map's or the
+// background's value where no point landed), the
 // epilogue's input x = I 2^-EV wb V(r) and the response's slope, and adds
 //   dL/dEV  += g R'(x) x (-ln 2)          dL/dwb_ch += g R'(x) I 2^-EV V
 //   dL/dc_v += g R'(x) I 2^-EV wb V'(r2) (-2 (p - c_v))
@@ -52,9 +53,11 @@ __global__ void __launch_bounds__(kThreads) k_photo_grad(const __grid_constant__
       const float r2 = ru * ru + rv * rv;
       const float vig = 1.0f + r2 * (cam.vig_a[0] + r2 * (cam.vig_a[1] + r2 * cam.vig_a[2]));
       const float dvig = cam.vig_a[0] + r2 * (2.0f * cam.vig_a[1] + 3.0f * r2 * cam.vig_a[2]);
+      float empty[C];
+      if (n == 0) empty_value<C>(cam, a, 0, u, v, empty);
 #pragma unroll
       for (int ch = 0; ch < (C < 3 ? C : 3); ++ch) {
-        const float I = n ? __fdiv_rn(cam.acc[p * C + ch], (float)n) : (a.background ? __ldg(a.background + ch) : 0.0f);
+        const float I = n ? __fdiv_rn(cam.acc[p * C + ch], (float)n) : empty[ch];
         const float g = __ldg(G + ch * np + p);
         int seg;
         float frac, slope;
@@ -135,6 +138,8 @@ adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, co
   if (n_cam < 1 || n_cam > ADOP_MAX_CAMERAS) return fail(ADOP_ERR_INVALID_ARG, "n_cam outside [1, 64]");
   if (!channels_supported(c)) return fail(ADOP_ERR_UNSUPPORTED, "channel count has no kernels");
   if (params->levels < 1 || params->levels > ADOP_MAX_LEVELS) return fail(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
+  if (params->env && !env_size_ok(params->env_w, params->env_h))
+    return fail(ADOP_ERR_INVALID_ARG, "env_w / env_h outside [1, 16384]");
   if (workspace_bytes < adop_photometric_workspace_bytes(n_cam) || !workspace || ((uintptr_t)workspace & 255))
     return fail(ADOP_ERR_INVALID_ARG, "workspace too small or not 256-byte aligned");
   size_t crf_off = 0;
@@ -168,10 +173,14 @@ adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, co
     pa.partials = partials;
     PointArgs a{};
     a.background = params->background;
+    a.env = params->env;
+    a.env_w = params->env_w;
+    a.env_h = params->env_h;
     a.levels = params->levels;
     a.ncam = nc;
     const size_t smem = sizeof(float) * 3 * (size_t)max_lut;
-    if ((e = launch_photo(lc, a, pa, c, smem, s)) != cudaSuccess) return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = timed("photo_grad", s, [&] { return launch_photo(lc, a, pa, c, smem, s); })) != cudaSuccess)
+      return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
     k_photo_reduce<<<nc, 32 * kPhotoParams, 0, s>>>(partials, kPhotoBlocks, grad_photo + (size_t)k0 * kPhotoParams);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
   }

@@ -201,6 +201,9 @@ void Server::launch_locked() {
     a.feat = P.feat;
     a.normals = (cfg.flags & ADOP_FLAG_NORMAL_CULL) ? P.normals : nullptr;
     a.background = cfg.background;
+    a.env = cfg.env;
+    a.env_w = cfg.env_w;
+    a.env_h = cfg.env_h;
     a.radius = nullptr;
     a.beta = nullptr;
     a.n = P.n;
@@ -289,6 +292,8 @@ adop_status adop_serve_create(const adop_serve_config* cfg, adop_server** out) {
     return err(ADOP_ERR_INVALID_ARG, "unknown output dtype");
   if (cfg->flags & ~(uint32_t)(ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL))
     return err(ADOP_ERR_INVALID_ARG, "server flags may only be ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL");
+  if (cfg->env && (!adop::env_size_ok(cfg->env_w, cfg->env_h) || ((uintptr_t)cfg->env & 3) != 0))
+    return err(ADOP_ERR_INVALID_ARG, "environment map size outside [1, 16384]^2 or misaligned");
   auto s = std::make_unique<Server>();
   s->cfg = *cfg;
   cudaError_t e = cudaMalloc(&s->pool, cfg->mem_budget_bytes);

@@ -7,6 +7,13 @@ Tolerances (relative, written from the arithmetic of each output):
   BF16 / FP16 image    the same with 2e-2 (one BF16 rounding of the output is 2^-9)
   per-point gradients  |gpu - ref| <= 1e-4 * max(|ref|, rms(ref)) per element
   pose / intrinsics    |gpu - ref| <= 1e-4 * sum over (point, layer) of |term|
+  with an environment map, pixels where no point lands hold a bilinear sample
+  whose texel coordinates the GPU computes in FP32 (inverse camera, rotation,
+  atan2 / acos): a direction error of at most ~4e-6 rad moves them by
+  (env_w / 2 pi + env_h / pi) 4e-6 texels, which for the maps used (64 x 128,
+  neighbouring texels within ~0.3, values ~0.5) is <= 5e-5 absolute, so the
+  image and gradients use 1e-4 there; dL/dE sums FP32 weights w G whose
+  weights carry the same coordinate error: 1e-3.
 """
 from __future__ import annotations
 
@@ -16,6 +23,8 @@ RTOL_FEAT_F32 = 1e-5
 RTOL_FEAT_LOWP = 2e-2
 RTOL_GRAD = 1e-4
 RTOL_REDUCED = 1e-4
+RTOL_ENV_IMG = 1e-4
+RTOL_ENV_GRAD = 1e-3
 
 U64_MAX = np.iinfo(np.uint64).max
 
@@ -67,7 +76,7 @@ def to_np(t):
 
 def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, flags=0,
             grads=None, out_dtype="f32", keep_state=True, backward=True, normals=False, crf=True,
-            grad_assign=False, init=0.0, vis=True, discard=None):
+            grad_assign=False, init=0.0, vis=True, discard=None, env=None):
     """Forward (+ backward) through the C ABI; returns numpy results."""
     import torch
     dev = "cuda"
@@ -80,7 +89,8 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
     bg = None if background is None else torch.tensor(np.asarray(background, np.float32), device=dev)
     if grad_assign:
         flags |= adop.ADOP_FLAG_GRAD_ASSIGN
-    params = adop.Params(levels, alpha, znear, bg, flags, 1.5 if discard is None else discard[2])
+    env_t = None if env is None else torch.from_numpy(np.ascontiguousarray(env, np.float32)).to(dev)
+    params = adop.Params(levels, alpha, znear, bg, flags, 1.5 if discard is None else discard[2], env_t)
     luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(dev)
             if (crf and getattr(c, "crf", None) is not None) else None for c in cams]
     frames = [adop.Frame.alloc(c, scene.c, levels, torch_dtype(out_dtype), keep_state, dev,
@@ -105,22 +115,29 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
         out["dxyz"] = gxyz.cpu().numpy().astype(np.float64) - init
         out["dpose"] = gpose.cpu().numpy().astype(np.float64) - init
         out["dintr"] = gintr.cpu().numpy().astype(np.float64) - init
+        if env is not None and keep_state:
+            genv = torch.zeros_like(env_t)
+            adop.adop_env_backward(cams, params, c, frames, gimgs, genv, crf_luts=luts)
+            torch.cuda.synchronize()
+            out["denv"] = genv.cpu().numpy().astype(np.float64)
     torch.cuda.synchronize()
     return out
 
 
 def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
                normals=False, epilogue=False, all_projected=False, backward=True, discard=None, leaky=False,
-               log_desc=False):
+               log_desc=False, env=None):
     """The oracle on the same inputs: per camera forward (+ backward), summed
     over cameras for the per-point gradients."""
     feat = scene.feat_as(dtype)
     res = {"keys": [], "cnt": [], "img": [], "dpose": [], "dintr": [], "dpose_abs": [], "dintr_abs": []}
     dfeat = np.zeros((scene.n, scene.c))
     dxyz = np.zeros((scene.n, 3))
+    denv = None if env is None else np.zeros(np.shape(env))
     for k, cam in enumerate(cams):
         kw = {} if discard is None else {"radius": discard[0], "beta": discard[1], "gamma": discard[2]}
         kw["log_desc"] = log_desc
+        kw["env"] = None if env is None else np.asarray(env, np.float64)
         f = orc.forward(scene.xyz, feat, cam, levels, alpha, znear, background,
                         scene.normals if normals else None, **kw)
         res["keys"].append(f.keys)
@@ -137,19 +154,26 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
                 G[:c * h * w] *= dgain.ravel()
         res["img"].append(img)
         if backward and G is not None:
+            if env is not None:
+                denv += orc.env_grad(f, cam, G, denv.shape)
             b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected, log_desc)
             dfeat += b.dfeat
             dxyz += b.dxyz
             for key in ("dpose", "dintr", "dpose_abs", "dintr_abs"):
                 res[key].append(getattr(b, key))
     res["dfeat"], res["dxyz"] = dfeat, dxyz
+    if denv is not None:
+        res["denv"] = denv
     return res
 
 
-def compare(gpu, ref, dtype="f32", out_dtype="f32", check_state=True, backward=True):
+def compare(gpu, ref, dtype="f32", out_dtype="f32", check_state=True, backward=True, env=False):
     """Assert parity of every output; returns the measured relative errors."""
     errs = {}
     rt_img = RTOL_FEAT_F32 if out_dtype == "f32" else RTOL_FEAT_LOWP
+    rt_grad = RTOL_GRAD
+    if env:
+        rt_img, rt_grad = max(rt_img, RTOL_ENV_IMG), max(RTOL_GRAD, RTOL_ENV_IMG)
     for k in range(len(ref["img"])):
         if check_state:
             assert np.array_equal(gpu["keys"][k], ref["keys"][k]), \
@@ -157,8 +181,10 @@ def compare(gpu, ref, dtype="f32", out_dtype="f32", check_state=True, backward=T
             assert np.array_equal(gpu["cnt"][k], ref["cnt"][k]), f"camera {k}: counts differ"
         errs[f"img{k}"] = assert_close(gpu["img"][k], ref["img"][k], rt_img, f"camera {k} image")
     if backward:
-        errs["dfeat"] = assert_close(gpu["dfeat"], ref["dfeat"], RTOL_GRAD, "dL/dtau")
-        errs["dxyz"] = assert_close(gpu["dxyz"], ref["dxyz"], RTOL_GRAD, "dL/dx")
+        errs["dfeat"] = assert_close(gpu["dfeat"], ref["dfeat"], rt_grad, "dL/dtau")
+        errs["dxyz"] = assert_close(gpu["dxyz"], ref["dxyz"], rt_grad, "dL/dx")
+        if "denv" in ref and "denv" in gpu:
+            errs["denv"] = assert_close(gpu["denv"], ref["denv"], RTOL_ENV_GRAD, "dL/dE")
         for k in range(len(ref["dpose"])):
             assert_reduced(gpu["dpose"][k], ref["dpose"][k], ref["dpose_abs"][k], what=f"camera {k} dL/dxi")
             assert_reduced(gpu["dintr"][k], ref["dintr"][k], ref["dintr_abs"][k], what=f"camera {k} dL/dK")

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
     for name in names:
         assert hasattr(so, name), f"{name} declared in include/ but not exported"
     assert set(names) <= set(adop.SIGNATURES), "binding misses a declared entry point"
-    assert adop.adop_abi_version() == 1
+    assert adop.adop_abi_version() == 2
 
 
 def _structs(adop, n=10, c=4, levels=4, w=64, h=48, flags=0):
@@ -69,6 +69,7 @@ def test_workspace_bytes(lib):
     ("znear", 1, "znear"), ("flags", 1, "flag"), ("cull", 1, "normals"), ("size", 1, "image size"),
     ("small", 1, "too small"), ("ws", 3, "workspace"), ("wsalign", 1, "aligned"), ("feat", 1, "16-byte"),
     ("mixed", 1, "all set or all NULL"), ("nan", 1, "non-finite"), ("dtype", 1, "dtype"),
+    ("envsize", 1, "environment map"), ("envalign", 1, "env must be 4-byte aligned"),
 ])
 def test_invalid_arguments_fail_synchronously(lib, case, status, msg):
     adop, so = lib
@@ -104,6 +105,10 @@ def test_invalid_arguments_fail_synchronously(lib, case, status, msg):
         cam[0].T.t[1] = float("inf")
     elif case == "dtype":
         fr[0].out_dtype = 7
+    elif case == "envsize":
+        prm.env, prm.env_w, prm.env_h = 0x50000, 64, 0
+    elif case == "envalign":
+        prm.env, prm.env_w, prm.env_h = 0x50002, 64, 32
     st = _fwd(so, pts, cam, prm, fr, **kw)
     assert st == status
     assert msg in so.adop_last_error().decode()
@@ -116,3 +121,21 @@ def test_backward_validates_too(lib):
     st = so.adop_render_backward(ct.byref(pts), cam, 1, ct.byref(prm), fr, None, None, None, None, None,
                                  0x100000, 1 << 40, None)
     assert st == 1 and "levels" in so.adop_last_error().decode()
+
+
+def test_env_backward_validates(lib):
+    adop, so = lib
+    pts, cam, prm, fr = _structs(adop)
+    g = ct.c_void_p(0x60000)
+    # no environment map in the params
+    st = so.adop_env_backward(cam, 1, ct.byref(prm), 8, fr, None, g, None)
+    assert st == 1 and "env" in so.adop_last_error().decode()
+    prm.env, prm.env_w, prm.env_h = 0x50000, 20000, 16
+    st = so.adop_env_backward(cam, 1, ct.byref(prm), 8, fr, None, g, None)
+    assert st == 1 and "16384" in so.adop_last_error().decode()
+    prm.env_w = 64
+    st = so.adop_env_backward(cam, 1, ct.byref(prm), 5, fr, None, g, None)
+    assert st == 2
+    # frames without the forward's counts
+    st = so.adop_env_backward(cam, 1, ct.byref(prm), 8, fr, None, g, None)
+    assert st == 1 and "count" in so.adop_last_error().decode()
