@@ -275,7 +275,8 @@ class Workload:
         self.env = self.genv = None
         if env:
             # the paper's 1024^2 spherical map of neural features, read as equirectangular
-            self.env = torch.from_numpy(scenes.env_map(self.c, 1024, 1024, seed=2025)).to(device)
+            E = scenes.env_map(self.c, 1024, 1024, seed=2025)
+            self.env = torch.from_numpy(np.ascontiguousarray(np.moveaxis(E, 0, -1))).to(device)
             self.genv = torch.zeros_like(self.env)
         self.params = adop.Params(LEVELS, 0.01, 1e-3, None, flags, 1.5, self.env)
         self.frame = adop.Frame.alloc(cam, self.c, LEVELS, tdt, True, device, self.n)

@@ -131,8 +131,10 @@ typedef struct {
  * threshold of Eq. depthtest (the paper uses 0.01); znear: points with
  * depth z <= znear are discarded; background: c FP32 values (device) shown
  * where no point lands when there is no environment map, NULL = zeros.
- * env (Sec. 3.1, environment map; NULL = none): c x env_h x env_w FP32
- * planar (device), an equirectangular map of world directions.  A pixel
+ * env (Sec. 3.1, environment map; NULL = none): env_h x env_w texels of c
+ * FP32 each, texel-major (texel (i, j) at env[(j env_w + i) c], channels
+ * contiguous; device, 16-byte aligned), an equirectangular map of world
+ * directions.  A pixel
  * where no point lands shows E(R^T C^-1(u0, v0)) instead of the background:
  * the ray through the pixel centre (layer-l pixel (p, q) at layer-0
  * coordinates (p 2^l, q 2^l)), C^-1 the inverse camera model (pinhole:
@@ -166,8 +168,9 @@ typedef struct {
  * (NULL = layer not written).  key[l] (uint64 per pixel: bits(z_min) << 32 |
  * index of the nearest point; UINT64_MAX when empty), count[l] (|Lambda|
  * per pixel) and acc (FP32 feature sums, pixel-major: pixel p of layer l at
- * acc[(off_l + p) * c], off_l = sum_{k<l} w_k h_k) are the per-pixel state
- * that the backward pass re-uses.  Either all of key/count/acc are given
+ * acc[(off_l + p) * c], off_l = sum_{k<l} w_k h_k; with an environment map,
+ * an empty pixel's acc holds the value the forward sampled for it) are the
+ * per-pixel state that the backward pass re-uses.  Either all of key/count/acc are given
  * (the forward fills them; the backward reads them) or all are NULL (the
  * forward keeps them in the workspace; the backward re-renders them there,
  * as the paper's backward pass does).
@@ -344,14 +347,15 @@ adop_status adop_serve_destroy(adop_server* s);
  */
 /*
  * Gradient of the environment map (Sec. 3.1), accumulated (+=) into
- * grad_env (c x env_h x env_w FP32, device): every pixel of every layer where
- * no point landed adds its upstream gradient to the four texels it sampled,
- * with the bilinear weights.  grad_image[k * levels + l] as in
+ * grad_env (laid out like params->env, 16-byte aligned): every pixel of every
+ * layer where no point landed adds its upstream gradient to the four texels
+ * it sampled, with the bilinear weights.  grad_image[k * levels + l] as in
  * adop_render_backward (at layer 0 it is chained through the photometric
- * epilogue when that is on); frames must carry the forward's count[l] of
- * every layer.  params->env must be the map the forward sampled.  Needs no
- * workspace.  Texel sums use FP32 atomics: their order, and so the last bits,
- * vary between runs.
+ * epilogue when that is on, at the value kept in frames[k].acc if given, else
+ * at a new sample); frames must carry the forward's count[l] of every layer.
+ * params->env must be the map the forward sampled.  Needs no workspace.
+ * Texel sums use FP32 atomics: their order, and so the last bits, vary
+ * between runs.
  */
 adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam, const adop_params* params, int32_t c,
                               const adop_frame* frames, const float* const* grad_image, float* grad_env,

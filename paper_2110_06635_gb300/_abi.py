@@ -172,10 +172,10 @@ class Params:
     background: object = None  # c float32 CUDA tensor or None
     flags: int = 0
     gamma: float = 1.5         # stochastic discarding (with ADOP_FLAG_DISCARD)
-    env: object = None         # c x env_h x env_w float32 CUDA tensor (environment map) or None
+    env: object = None         # env_h x env_w x c float32 CUDA tensor (environment map) or None
 
     def struct(self) -> adop_params:
-        eh, ew = (0, 0) if self.env is None else (int(self.env.shape[-2]), int(self.env.shape[-1]))
+        eh, ew = (0, 0) if self.env is None else (int(self.env.shape[0]), int(self.env.shape[1]))
         return adop_params(self.levels, self.alpha, self.znear, _dev_ptr(self.background), self.flags, self.gamma,
                            _dev_ptr(self.env), ew, eh)
 
@@ -473,7 +473,7 @@ class Server:
         self._clouds = []
         self._bg = background
         self._env = env
-        eh, ew = (0, 0) if env is None else (int(env.shape[-2]), int(env.shape[-1]))
+        eh, ew = (0, 0) if env is None else (int(env.shape[0]), int(env.shape[1]))
         cfg = adop_serve_config(mem_budget_bytes, max_slots, streams, max_batch, levels, alpha, znear, flags,
                                 dtype_code(self.out_dtype), _dev_ptr(background), _dev_ptr(env), ew, eh)
         h = ct.c_void_p()

@@ -13,8 +13,9 @@ camera's image pyramid and makes it differentiable with respect to
   dL/dxi exactly at xi = 0,
 * ``intrinsics`` (n_cam x 6: fx, fy, cx, cy, k1, k2), replacing the cameras'
   values,
-* ``env`` (c x env_h x env_w float32, the environment map that pixels where
-  no point lands show, Sec. 3.1); its gradient needs ``keep_state=True``.
+* ``env`` (env_h x env_w x c float32, texel-major: the environment map that
+  pixels where no point lands show, Sec. 3.1); its gradient needs
+  ``keep_state=True``.
 
 ``keep_state=True`` keeps each camera's per-pixel key/count/sum buffers and
 per-point layer mask for the backward pass; ``keep_state=False`` keeps only
@@ -144,7 +145,7 @@ def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01
     """Differentiable render of every camera; returns [camera][layer] images
     (c x h_l x w_l).  See the module docstring for the gradients.  With
     radius and beta (float32 per point), stochastic point discarding
-    (Eq. discard) with threshold gamma; with env (c x env_h x env_w float32),
+    (Eq. discard) with threshold gamma; with env (env_h x env_w x c float32),
     empty pixels sample the environment map."""
     cams = _effective_cameras(cameras, xi, intrinsics)
     if radius is not None:

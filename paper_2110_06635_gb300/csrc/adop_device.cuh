@@ -28,6 +28,7 @@ struct DevCam {
   float R[9];
   float t[3];
   float fx, fy, cx, cy, k1, k2, k3, p1, p2;
+  float ifx, ify;  // f32(1 / fx), f32(1 / fy) (the inverse camera)
   int32_t w, h;
   int32_t model;  // 0 pinhole + Brown-Conrady, 1 fisheye (stereographic)
   int64_t off[ADOP_MAX_LEVELS + 1];  // first pixel of each layer in the concatenated pyramid
@@ -53,6 +54,9 @@ struct DevCam {
   float vig_c[2];
   float vig_a[3];
   const float* crf;
+  // environment map gradient: acc holds each empty pixel's sampled value
+  // (the caller passed the forward's kept state)
+  int32_t env_in_acc;
 };
 
 struct LaunchCams {
@@ -98,6 +102,22 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ src, float* d
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) dst[k] = __ldg(src + k);
+  }
+}
+
+// Store n floats to a suitably aligned address with the widest vector stores.
+template <int N>
+__device__ __forceinline__ void store_vec(float* dst, const float* src) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 4; ++v)
+      reinterpret_cast<float4*>(dst)[v] = make_float4(src[4 * v], src[4 * v + 1], src[4 * v + 2], src[4 * v + 3]);
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 2; ++v) reinterpret_cast<float2*>(dst)[v] = make_float2(src[2 * v], src[2 * v + 1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[k] = src[k];
   }
 }
 
@@ -353,43 +373,59 @@ __device__ __forceinline__ float epilogue(const DevCam& cam, int ch, int32_t u, 
 
 constexpr int kInvertSteps = 20;  // fixed-point / Newton steps of the inverse camera
 
+// Newton steps on r radial(r^2) = r_d, radial(s) = 1 + s (k1 + s (k2 + s k3)):
+// the undistorted normalised radius of a distorted one (both camera models
+// share the radial polynomial).  Converges in a few steps for the moderate
+// distortion of calibrated lenses; stops when a step is below 1e-7 r.
+__device__ __forceinline__ float undistort_radius(const DevCam& cam, float rd) {
+  float r = rd;
+  for (int it = 0; it < kInvertSteps; ++it) {
+    const float r2 = r * r;
+    const float f = r * (1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3))) - rd;
+    const float fp = 1.0f + r2 * (3.0f * cam.k1 + r2 * (5.0f * cam.k2 + r2 * 7.0f * cam.k3));
+    const float step = __fdividef(f, fp);
+    r -= step;
+    if (!(fabsf(step) > 1e-7f * r)) break;
+  }
+  return r;
+}
+
 // Inverse camera model C^-1: the unit camera-space direction of the ray
-// through layer-0 pixel coordinates (u0, v0).  Pinhole: the Brown-Conrady
-// distortion is undone by fixed-point steps (xn, yn) <- ((xd, yd) -
+// through layer-0 pixel coordinates (u0, v0).  Radial distortion only (the
+// fisheye, and the pinhole with p1 = p2 = 0): Newton on the radius; with
+// tangential terms, fixed-point steps (xn, yn) <- ((xd, yd) -
 // tangential(xn, yn)) / radial(xn, yn), which contract for the moderate
-// distortion of calibrated lenses; fisheye: Newton steps on
-// r radial(r^2) = r_d, then the inverse stereographic map
-// (xn, yn) -> (4 xn, 4 yn, 4 - r^2) / (4 + r^2).  FP32.
+// distortion of calibrated lenses.  The fisheye then inverts the
+// stereographic map, (xn, yn) -> (4 xn, 4 yn, 4 - r^2) / (4 + r^2).  FP32.
 __device__ __forceinline__ void camera_inverse(const DevCam& cam, float u0, float v0, float (&d)[3]) {
-  const float xd = (u0 - cam.cx) / cam.fx, yd = (v0 - cam.cy) / cam.fy;
-  if (cam.model == 1) {
+  const float xd = (u0 - cam.cx) * cam.ifx, yd = (v0 - cam.cy) * cam.ify;
+  float xn = xd, yn = yd;
+  if (cam.model == 1 || (cam.p1 == 0.0f && cam.p2 == 0.0f)) {
     const float rd = sqrtf(xd * xd + yd * yd);
-    float r = rd;
-#pragma unroll 4
+    const float s = rd > 0.0f ? __fdividef(undistort_radius(cam, rd), rd) : 1.0f;
+    xn = xd * s;
+    yn = yd * s;
+  } else {
     for (int it = 0; it < kInvertSteps; ++it) {
-      const float r2 = r * r;
-      const float f = r * (1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3))) - rd;
-      const float fp = 1.0f + r2 * (3.0f * cam.k1 + r2 * (5.0f * cam.k2 + r2 * 7.0f * cam.k3));
-      r -= f / fp;
+      const float r2 = xn * xn + yn * yn;
+      const float rad = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
+      const float tx = 2.0f * cam.p1 * xn * yn + cam.p2 * (r2 + 2.0f * xn * xn);
+      const float ty = cam.p1 * (r2 + 2.0f * yn * yn) + 2.0f * cam.p2 * xn * yn;
+      const float inv = __fdividef(1.0f, rad);
+      const float nx = (xd - tx) * inv, ny = (yd - ty) * inv;
+      const bool still = fabsf(nx - xn) + fabsf(ny - yn) > 1e-7f * (fabsf(nx) + fabsf(ny) + 1e-3f);
+      xn = nx;
+      yn = ny;
+      if (!still) break;
     }
-    const float s = rd > 0.0f ? r / rd : 1.0f;
-    const float xn = xd * s, yn = yd * s;
+  }
+  if (cam.model == 1) {
     const float r2 = xn * xn + yn * yn;
-    const float inv = 1.0f / (4.0f + r2);
+    const float inv = __fdividef(1.0f, 4.0f + r2);
     d[0] = 4.0f * xn * inv;
     d[1] = 4.0f * yn * inv;
     d[2] = (4.0f - r2) * inv;
     return;
-  }
-  float xn = xd, yn = yd;
-#pragma unroll 4
-  for (int it = 0; it < kInvertSteps; ++it) {
-    const float r2 = xn * xn + yn * yn;
-    const float rad = 1.0f + r2 * (cam.k1 + r2 * (cam.k2 + r2 * cam.k3));
-    const float tx = 2.0f * cam.p1 * xn * yn + cam.p2 * (r2 + 2.0f * xn * xn);
-    const float ty = cam.p1 * (r2 + 2.0f * yn * yn) + 2.0f * cam.p2 * xn * yn;
-    xn = (xd - tx) / rad;
-    yn = (yd - ty) / rad;
   }
   const float inv = rsqrtf(xn * xn + yn * yn + 1.0f);
   d[0] = xn * inv;
@@ -422,7 +458,11 @@ __device__ __forceinline__ EnvTaps env_taps(const DevCam& cam, int32_t ew, int32
   const float fu0 = floorf(ue), fv0 = floorf(ve);
   const float fu = ue - fu0, fv = ve - fv0;
   const int32_t iu0 = (int32_t)fu0, iv0 = (int32_t)fv0;
-  const int32_t ua = ((iu0 % ew) + ew) % ew;
+  // longitude lies in [-pi, pi], so iu0 is in [-1, ew - 1] up to rounding;
+  // the clamp keeps a NaN direction in range too
+  int32_t ua = iu0 < 0 ? iu0 + ew : iu0;
+  ua = ua >= ew ? ua - ew : ua;
+  ua = min(max(ua, 0), ew - 1);
   const int32_t ub = ua + 1 == ew ? 0 : ua + 1;
   const int32_t va = min(max(iv0, 0), eh - 1), vb = min(max(iv0 + 1, 0), eh - 1);
   EnvTaps e;
@@ -437,12 +477,19 @@ __device__ __forceinline__ EnvTaps env_taps(const DevCam& cam, int32_t ew, int32
   return e;
 }
 
-// Sampled value of channels [0, n) of env (c planes of ew x eh) at the taps.
-__device__ __forceinline__ float env_channel(const float* __restrict__ env, int64_t plane, const EnvTaps& e,
-                                             int ch) {
-  const float* E = env + ch * plane;
-  return e.w[0] * __ldg(E + e.t[0]) + e.w[1] * __ldg(E + e.t[1]) + e.w[2] * __ldg(E + e.t[2]) +
-         e.w[3] * __ldg(E + e.t[3]);
+// Bilinear sample of the C channels of a texel-major map (texel t's C
+// floats at env + t C) at the taps.
+template <int C>
+__device__ __forceinline__ void env_sample(const float* __restrict__ env, const EnvTaps& e, float (&v)[C]) {
+#pragma unroll
+  for (int k = 0; k < C; ++k) v[k] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float tx[C];
+    load_vec<C>(env + (int64_t)e.t[j] * C, tx);
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = fmaf(e.w[j], tx[k], v[k]);
+  }
 }
 
 }  // namespace adop

@@ -151,7 +151,7 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
   if (prm->env) {
     if (!env_size_ok(prm->env_w, prm->env_h))
       return fail(ADOP_ERR_INVALID_ARG, "environment map %dx%d outside [1, 16384]^2", prm->env_w, prm->env_h);
-    if (((uintptr_t)prm->env & 3) != 0) return fail(ADOP_ERR_INVALID_ARG, "env must be 4-byte aligned");
+    if (((uintptr_t)prm->env & 15) != 0) return fail(ADOP_ERR_INVALID_ARG, "env must be 16-byte aligned");
   }
   if ((prm->flags & ADOP_FLAG_NORMAL_CULL) && pts->n > 0 && !pts->normals)
     return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_NORMAL_CULL needs normals");
@@ -305,6 +305,10 @@ adop_status render_chunk(const adop_points* pts, const adop_camera* cams, int k0
       if ((e = timed("normalize", s, [&] { return launch_normalize(sub, sa, pts->c, (adop_dtype)dt, s); })) !=
           cudaSuccess)
         return cuda_fail(e, "normalize launch");
+      if (prm->env &&
+          (e = timed("env_fill", s, [&] { return launch_env_fill(sub, sa, pts->c, (adop_dtype)dt, s); })) !=
+              cudaSuccess)
+        return cuda_fail(e, "environment map launch");
     }
   }
   return ADOP_OK;
@@ -342,6 +346,8 @@ void set_camera_constants(DevCam& d, const adop_camera& cam, int levels, uint32_
   memcpy(d.t, cam.T.t, sizeof(d.t));
   d.fx = cam.K.fx; d.fy = cam.K.fy; d.cx = cam.K.cx; d.cy = cam.K.cy;
   d.k1 = cam.K.k1; d.k2 = cam.K.k2; d.k3 = cam.K.k3; d.p1 = cam.K.p1; d.p2 = cam.K.p2;
+  d.ifx = (float)(1.0 / (double)cam.K.fx);
+  d.ify = (float)(1.0 / (double)cam.K.fy);
   d.w = cam.K.w;
   d.h = cam.K.h;
   d.model = cam.K.model;
@@ -530,6 +536,9 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
         if ((e = timed("accumulate", s, [&] { return launch_accum(rc, a, pts->c, pts->feat_dtype, s); })) !=
             cudaSuccess)
           return cuda_fail(e, "accumulate launch");
+        if (params->env &&
+            (e = timed("env_fill", s, [&] { return launch_env_fill(rc, a, pts->c, ADOP_F32, s); })) != cudaSuccess)
+          return cuda_fail(e, "environment map launch");
       }
     }
     LaunchCams lc;

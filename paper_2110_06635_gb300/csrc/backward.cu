@@ -43,9 +43,12 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const uint32_t n = cam.cnt[l][p];
     const unsigned long long key = cam.key[l][p];
     float I[C], G[GS];
-    if (n == 0) {
-      const int32_t wl = cam.w >> l;
-      empty_value<C>(cam, a, l, (int32_t)(p % wl), (int32_t)(p / wl), I);
+    if (n == 0 && !a.env) {
+#pragma unroll
+      for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
+    } else if (n == 0) {  // the environment map's value, kept in acc by k_env_fill
+#pragma unroll
+      for (int k = 0; k < C; ++k) I[k] = cam.acc[g * C + k];
     } else {
       const float fn = (float)n;
 #pragma unroll

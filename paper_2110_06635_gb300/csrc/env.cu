@@ -1,9 +1,12 @@
-// Gradient of the environment map (Sec. 3.1).  An empty pixel's value is
-// the bilinear sample sum_j w_j E[t_j] along its ray, so dL/dE[t_j] gains
-// w_j G for every channel.  One thread per pyramid pixel; pixels with a point
-// return at once, the others recompute their taps (the inverse camera and the
-// equirectangular lookup of the forward), chain layer 0 through the
-// photometric epilogue and add to the four texels with FP32 atomics.
+// Environment map (Sec. 3.1).  An empty pixel shows the bilinear sample
+// sum_j w_j E[t_j] along its ray (env_taps: inverse camera, R^T, the
+// equirectangular lookup), so dL/dE[t_j] gains w_j G for every channel.
+//   k_env_fill  one thread per pyramid pixel: samples the map where no point
+//               landed, keeps the value in acc, writes the image pixel.
+//   k_env_grad  one thread per pyramid pixel: recomputes the taps, chains
+//               layer 0 through the photometric epilogue and adds w_j G with
+//               FP32 vector atomics (the map is texel-major: a texel's C
+//               floats are contiguous).
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -11,12 +14,45 @@
 namespace adop {
 namespace {
 
+// Sample the map for every empty pixel: the value goes to acc (the pixel
+// state the backward pass reads) and, where the layer's image is written, to
+// the image (through the photometric epilogue at layer 0).
+template <int C, typename TO>
+__global__ void __launch_bounds__(kThreads) k_env_fill(const __grid_constant__ LaunchCams cams,
+                                                       const __grid_constant__ PointArgs a) {
+  const DevCam& cam = cams.c[blockIdx.y];
+  const int64_t total = cam.off[a.levels];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int l = layer_of(cam, a.levels, g);
+    const int64_t p = g - cam.off[l];
+    if (cam.cnt[l][p] != 0) continue;
+    const int32_t wl = cam.w >> l, pi = (int32_t)p;  // a pyramid has fewer than 2^31 pixels
+    const int32_t pu = pi % wl, pv = pi / wl;
+    float v[C];
+    env_sample<C>(a.env, env_taps(cam, a.env_w, a.env_h, l, pu, pv), v);
+    store_vec<C>(cam.acc + g * C, v);
+    TO* img = reinterpret_cast<TO*>(cam.image[l]);
+    if (img == nullptr) continue;
+    if (l == 0 && cam.epi) {
+#pragma unroll
+      for (int k = 0; k < (C < 3 ? C : 3); ++k) v[k] = epilogue(cam, k, pu, pv, v[k], nullptr);
+    }
+    const int64_t np = cam.off[l + 1] - cam.off[l];
+#pragma unroll
+    for (int k = 0; k < C; ++k) img[k * np + p] = from_f32<TO>(v[k]);
+  }
+}
+
+// dL/dE: each empty pixel adds w_j G to its four texels with FP32 vector
+// atomics.  (Summing runs of equal taps across the warp first was measured
+// slower: the shuffles cost more instructions and registers than the
+// atomics they saved.)
 template <int C>
 __global__ void __launch_bounds__(kThreads) k_env_grad(const __grid_constant__ LaunchCams cams,
                                                        const __grid_constant__ PointArgs a, float* grad_env) {
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
-  const int64_t plane = (int64_t)a.env_w * a.env_h;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int l = layer_of(cam, a.levels, g);
@@ -24,27 +60,33 @@ __global__ void __launch_bounds__(kThreads) k_env_grad(const __grid_constant__ L
     const int64_t p = g - cam.off[l];
     if (gl == nullptr || cam.cnt[l][p] != 0) continue;
     const int64_t np = cam.off[l + 1] - cam.off[l];
-    const int32_t wl = cam.w >> l;
-    const int32_t pu = (int32_t)(p % wl), pv = (int32_t)(p / wl);
+    const int32_t wl = cam.w >> l, pi = (int32_t)p;
+    const int32_t pu = pi % wl, pv = pi / wl;
     const EnvTaps e = env_taps(cam, a.env_w, a.env_h, l, pu, pv);
     float G[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) G[k] = __ldg(gl + k * np + p);
     if (l == 0 && cam.epi) {
+      float I[C];
+      if (cam.env_in_acc) {
+        load_vec<C>(cam.acc + g * C, I);
+      } else {
+        env_sample<C>(a.env, e, I);
+      }
 #pragma unroll
       for (int k = 0; k < (C < 3 ? C : 3); ++k) {
         float d;
-        epilogue(cam, k, pu, pv, env_channel(a.env, plane, e, k), &d);
+        epilogue(cam, k, pu, pv, I[k], &d);
         G[k] *= d;
       }
     }
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-      if (G[k] == 0.0f) continue;
-      float* dst = grad_env + k * plane;
+    for (int j = 0; j < 4; ++j) {
+      if (e.w[j] == 0.0f) continue;
+      float wg[C];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (e.w[j] != 0.0f) atomicAdd(dst + e.t[j], e.w[j] * G[k]);
+      for (int k = 0; k < C; ++k) wg[k] = e.w[j] * G[k];
+      atomic_add_vec<C>(grad_env + (int64_t)e.t[j] * C, wg);
     }
   }
 }
@@ -55,6 +97,11 @@ adop_status fail(adop_status st, const char* msg) {
 }
 
 }  // namespace
+
+cudaError_t launch_env_fill(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, k_env_fill<kC, TO><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a)));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s) {
   ADOP_DISPATCH_C(c, k_env_grad<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a, grad_env));
@@ -72,8 +119,8 @@ extern "C" adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam,
   if (!params->env) return fail(ADOP_ERR_INVALID_ARG, "params->env is NULL: no environment map to differentiate");
   if (!env_size_ok(params->env_w, params->env_h))
     return fail(ADOP_ERR_INVALID_ARG, "env_w / env_h outside [1, 16384]");
-  if (((uintptr_t)params->env & 3) != 0 || ((uintptr_t)grad_env & 3) != 0)
-    return fail(ADOP_ERR_INVALID_ARG, "env / grad_env must be 4-byte aligned");
+  if (((uintptr_t)params->env & 15) != 0 || ((uintptr_t)grad_env & 15) != 0)
+    return fail(ADOP_ERR_INVALID_ARG, "env / grad_env must be 16-byte aligned");
   if (n_cam < 1 || n_cam > ADOP_MAX_CAMERAS) return fail(ADOP_ERR_INVALID_ARG, "n_cam outside [1, 64]");
   if (!channels_supported(c)) return fail(ADOP_ERR_UNSUPPORTED, "channel count has no kernels");
   if (params->levels < 1 || params->levels > ADOP_MAX_LEVELS) return fail(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
@@ -95,6 +142,8 @@ extern "C" adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam,
     for (int j = 0; j < nc; ++j) {
       const int k = k0 + j;
       set_camera_constants(lc.c[j], cams[k], params->levels, params->flags);
+      lc.c[j].acc = frames[k].acc;
+      lc.c[j].env_in_acc = frames[k].acc != nullptr ? 1 : 0;
       for (int l = 0; l < params->levels; ++l) {
         lc.c[j].cnt[l] = frames[k].count[l];
         lc.c[j].grad[l] = grad_image ? grad_image[(size_t)k * params->levels + l] : nullptr;

@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
 }
 
 // ---------------------------------------------------------------------------
-// K3 normalise: I = sum / |Lambda| (Eq. blend), environment map or background where empty,
+// K3 normalise: I = sum / |Lambda| (Eq. blend), background where empty (k_env_fill
+// writes the environment map's pixels),
 // photometric epilogue on layer 0, cast to the output type, planar layout
 // ---------------------------------------------------------------------------
 template <int C, typename TO>
@@ -156,8 +157,9 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ 
     const uint32_t n = cam.cnt[l][p];
     float v[C];
     if (n == 0) {
-      const int32_t wl = cam.w >> l;
-      empty_value<C>(cam, a, l, (int32_t)(p % wl), (int32_t)(p / wl), v);
+      if (a.env) continue;  // the environment map's pixels: k_env_fill
+#pragma unroll
+      for (int k = 0; k < C; ++k) v[k] = a.background ? __ldg(a.background + k) : 0.0f;
     } else {
       const float* acc = cam.acc + g * C;
       const float fn = (float)n;

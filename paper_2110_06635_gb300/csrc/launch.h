@@ -14,7 +14,7 @@ struct PointArgs {
   const void* feat;
   const float* normals;  // non-NULL only when normal culling is on
   const float* background;
-  const float* env;     // environment map (NULL = background): c x env_h x env_w
+  const float* env;     // environment map (NULL = background): env_h x env_w texels of c floats
   int32_t env_w, env_h;
   const float* radius;  // stochastic discarding (NULL = off): world radius per point
   const float* beta;    // and uniform draw per point
@@ -57,22 +57,11 @@ cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s);
 
-// Value of an empty layer-l pixel (pu, pv): the environment map's sample
-// along the pixel's ray, else the background (else zero).
-template <int C>
-__device__ __forceinline__ void empty_value(const DevCam& cam, const PointArgs& a, int l, int32_t pu, int32_t pv,
-                                            float (&v)[C]) {
-  if (a.env) {
-    const EnvTaps e = env_taps(cam, a.env_w, a.env_h, l, pu, pv);
-    const int64_t plane = (int64_t)a.env_w * a.env_h;
-#pragma unroll
-    for (int k = 0; k < C; ++k) v[k] = env_channel(a.env, plane, e, k);
-  } else {
-#pragma unroll
-    for (int k = 0; k < C; ++k) v[k] = a.background ? __ldg(a.background + k) : 0.0f;
-  }
-}
-
+// Environment map (a.env non-NULL): k_env_fill samples it for every empty
+// pixel, stores the value in acc (where the backward pass and the
+// photometric gradients read it) and, where image[l] is set, writes the
+// pixel (through the epilogue at layer 0); k_env_grad scatters dL/dE.
+cudaError_t launch_env_fill(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s);
 cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s);
 
 // Pixels of a w x h pyramid of `levels` layers (w_l = w >> l, h_l = h >> l);

@@ -54,7 +54,13 @@ __global__ void __launch_bounds__(kThreads) k_photo_grad(const __grid_constant__
       const float vig = 1.0f + r2 * (cam.vig_a[0] + r2 * (cam.vig_a[1] + r2 * cam.vig_a[2]));
       const float dvig = cam.vig_a[0] + r2 * (2.0f * cam.vig_a[1] + 3.0f * r2 * cam.vig_a[2]);
       float empty[C];
-      if (n == 0) empty_value<C>(cam, a, 0, u, v, empty);
+      if (n == 0 && a.env) {  // the environment map's value, kept in acc by the forward
+#pragma unroll
+        for (int k = 0; k < C; ++k) empty[k] = cam.acc[p * C + k];
+      } else if (n == 0) {
+#pragma unroll
+        for (int k = 0; k < C; ++k) empty[k] = a.background ? __ldg(a.background + k) : 0.0f;
+      }
 #pragma unroll
       for (int ch = 0; ch < (C < 3 ? C : 3); ++ch) {
         const float I = n ? __fdiv_rn(cam.acc[p * C + ch], (float)n) : empty[ch];

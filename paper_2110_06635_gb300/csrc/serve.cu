@@ -217,6 +217,7 @@ void Server::launch_locked() {
     if (e == cudaSuccess) e = launch_depth(lc, a, st);
     if (e == cudaSuccess) e = launch_accum(lc, a, c, feat_dtype, st);
     if (e == cudaSuccess) e = launch_normalize(lc, a, c, cfg.out_dtype, st);
+    if (e == cudaSuccess && cfg.env) e = launch_env_fill(lc, a, c, cfg.out_dtype, st);
     auto bt = std::make_unique<Batch>();
     bt->tickets = pick;
     bt->stream = s;
@@ -292,7 +293,7 @@ adop_status adop_serve_create(const adop_serve_config* cfg, adop_server** out) {
     return err(ADOP_ERR_INVALID_ARG, "unknown output dtype");
   if (cfg->flags & ~(uint32_t)(ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL))
     return err(ADOP_ERR_INVALID_ARG, "server flags may only be ADOP_FLAG_EPILOGUE | ADOP_FLAG_NORMAL_CULL");
-  if (cfg->env && (!adop::env_size_ok(cfg->env_w, cfg->env_h) || ((uintptr_t)cfg->env & 3) != 0))
+  if (cfg->env && (!adop::env_size_ok(cfg->env_w, cfg->env_h) || ((uintptr_t)cfg->env & 15) != 0))
     return err(ADOP_ERR_INVALID_ARG, "environment map size outside [1, 16384]^2 or misaligned");
   auto s = std::make_unique<Server>();
   s->cfg = *cfg;

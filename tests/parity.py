@@ -89,7 +89,9 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
     bg = None if background is None else torch.tensor(np.asarray(background, np.float32), device=dev)
     if grad_assign:
         flags |= adop.ADOP_FLAG_GRAD_ASSIGN
-    env_t = None if env is None else torch.from_numpy(np.ascontiguousarray(env, np.float32)).to(dev)
+    # the library's map is texel-major (h x w x c); the oracle's is planar (c x h x w)
+    env_t = None if env is None else \
+        torch.from_numpy(np.ascontiguousarray(np.moveaxis(np.asarray(env, np.float32), 0, -1))).to(dev)
     params = adop.Params(levels, alpha, znear, bg, flags, 1.5 if discard is None else discard[2], env_t)
     luts = [torch.from_numpy(np.ascontiguousarray(c.crf, np.float32)).to(dev)
             if (crf and getattr(c, "crf", None) is not None) else None for c in cams]
@@ -119,7 +121,7 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
             genv = torch.zeros_like(env_t)
             adop.adop_env_backward(cams, params, c, frames, gimgs, genv, crf_luts=luts)
             torch.cuda.synchronize()
-            out["denv"] = genv.cpu().numpy().astype(np.float64)
+            out["denv"] = np.moveaxis(genv.cpu().numpy().astype(np.float64), -1, 0)
     torch.cuda.synchronize()
     return out
 

@@ -69,7 +69,7 @@ def test_workspace_bytes(lib):
     ("znear", 1, "znear"), ("flags", 1, "flag"), ("cull", 1, "normals"), ("size", 1, "image size"),
     ("small", 1, "too small"), ("ws", 3, "workspace"), ("wsalign", 1, "aligned"), ("feat", 1, "16-byte"),
     ("mixed", 1, "all set or all NULL"), ("nan", 1, "non-finite"), ("dtype", 1, "dtype"),
-    ("envsize", 1, "environment map"), ("envalign", 1, "env must be 4-byte aligned"),
+    ("envsize", 1, "environment map"), ("envalign", 1, "env must be 16-byte aligned"),
 ])
 def test_invalid_arguments_fail_synchronously(lib, case, status, msg):
     adop, so = lib
@@ -108,7 +108,7 @@ def test_invalid_arguments_fail_synchronously(lib, case, status, msg):
     elif case == "envsize":
         prm.env, prm.env_w, prm.env_h = 0x50000, 64, 0
     elif case == "envalign":
-        prm.env, prm.env_w, prm.env_h = 0x50002, 64, 32
+        prm.env, prm.env_w, prm.env_h = 0x50008, 64, 32
     st = _fwd(so, pts, cam, prm, fr, **kw)
     assert st == status
     assert msg in so.adop_last_error().decode()

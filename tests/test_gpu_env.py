@@ -40,6 +40,17 @@ def test_env_forward_backward(adop, orc, dtype):
     assert np.abs(r["denv"]).max() > 0 and errs["denv"] <= RTOL_ENV_GRAD
 
 
+def test_env_without_kept_state(adop, orc):
+    # the backward re-renders the pixel state and samples the map itself
+    sc = scenes.tiny_spheres(6000, 4, seed=101)
+    cams = _cams()
+    env = scenes.env_map(4, 64, 128, seed=102)
+    G = [scenes.upstream_grad(c.w, c.h, 4, 4, 103 + k) for k, c in enumerate(cams)]
+    g = gpu_run(adop, sc, cams, "f32", grads=G, env=env, keep_state=False)
+    r = oracle_run(orc, sc, cams, "f32", grads=G, env=env)
+    compare(g, r, check_state=False, env=True)
+
+
 def test_env_fisheye(adop, orc):
     sc = scenes.tiny_spheres(6000, 4, seed=85)
     cams = _cams(model=1)
@@ -92,7 +103,7 @@ def test_env_in_the_server(adop):
     import torch
     sc = scenes.tiny_spheres(6000, 8, seed=96)
     cams = _cams()
-    env = torch.from_numpy(scenes.env_map(8, 64, 128, seed=97)).cuda()
+    env = torch.from_numpy(np.ascontiguousarray(np.moveaxis(scenes.env_map(8, 64, 128, seed=97), 0, -1))).cuda()
     pts = adop.Points(torch.from_numpy(sc.xyz).cuda(), torch.from_numpy(sc.feat).cuda())
     params = adop.Params(4, 0.01, 1e-3, None, 0, 1.5, env)
     srv = adop.Server(mem_budget_bytes=64 << 20, max_slots=4, streams=2, max_batch=2, levels=4, env=env)
@@ -119,7 +130,7 @@ def test_env_autograd(adop, orc):
     sc = scenes.tiny_spheres(6000, 4, seed=98)
     cams = _cams()
     env_np = scenes.env_map(4, 64, 128, seed=99)
-    env = torch.from_numpy(env_np).cuda().requires_grad_(True)
+    env = torch.from_numpy(np.ascontiguousarray(np.moveaxis(env_np, 0, -1))).cuda().requires_grad_(True)
     xyz = torch.from_numpy(sc.xyz).cuda()
     feat = torch.from_numpy(sc.feat).cuda()
     G = [scenes.upstream_grad(c.w, c.h, 4, 4, 100 + k) for k, c in enumerate(cams)]
@@ -128,4 +139,4 @@ def test_env_autograd(adop, orc):
                for k in range(len(cams)) for l, im in enumerate(imgs[k]))
     loss.backward()
     r = oracle_run(orc, sc, cams, "f32", grads=G, env=env_np, backward=True)
-    assert_close(env.grad.cpu().numpy(), r["denv"], RTOL_ENV_GRAD, "dL/dE through autograd")
+    assert_close(np.moveaxis(env.grad.cpu().numpy(), -1, 0), r["denv"], RTOL_ENV_GRAD, "dL/dE through autograd")
