@@ -345,19 +345,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
 // consecutive points, lists their (point, layer) pairs that are in Lambda in
 // shared memory and processes that list densely, one pair per lane, so that
 // lanes are not idle on the (majority of) occluded pairs.  Per-point sums
-// over layers go through shared-memory atomics; the owning lane then applies
-// the chain rule and writes its point's gradients.
+// over layers are segmented warp reductions (a point's pairs are consecutive
+// in the list); the owning lane then applies the chain rule and writes its
+// point's gradients.
 template <int C, typename TF, bool BINNED>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant__ LaunchCams cams,
                                                            const __grid_constant__ PointArgs a,
                                                            const __grid_constant__ BwdArgs b) {
   constexpr int GS = g_stride(C);
-  constexpr int PS = (3 + C) | 1;  // per point: z, u0, v0, tau (odd stride: no bank conflicts)
+  constexpr int PS = (6 + C) | 1;  // per point: z, u0, v0, X (camera space), tau (odd stride: no bank conflicts)
   constexpr int AS = (C + 2) | 1;  // per point: sum of G/|Lambda|, du0, dv0
   constexpr int kWarps = kThreads / 32;
   __shared__ float s_pt[kWarps][32 * PS];
   __shared__ float s_acc[kWarps][32 * AS];
   __shared__ uint8_t s_item[kWarps][32 * ADOP_MAX_LEVELS];
+  __shared__ float s_red[kWarps][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
@@ -367,9 +369,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
   float* acc = s_acc[warp];
   uint8_t* item = s_item[warp];
   const uint64_t pol = policy_evict_last();
-  float red[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) red[k] = 0.0f;
+  if (lane < 12) s_red[warp][lane] = 0.0f;  // pose / intrinsics sums of this warp
 
   // the points to visit: all, in index order, or the visible ones tile by tile
   const int64_t count = BINNED ? (int64_t)cam.bin_off[cam.tiles] : a.n;
@@ -378,18 +378,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
     const int64_t j = base + lane;
     const int64_t i = j < count ? (BINNED ? (int64_t)__ldcs(cam.bin_list + j) : j) : a.n;
     const uint32_t mask = i < a.n ? (__ldcs(cam.vis + i) & 0xFFu) : 0u;
-    float X0 = 0.f, X1 = 0.f, X2 = 1.f;
     if (mask) {
-      float u0 = 0.0f, v0 = 0.0f, zd = 0.0f;
+      float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd = 0.0f;
       transform(cam, __ldcs(a.xyz + 3 * i), __ldcs(a.xyz + 3 * i + 1), __ldcs(a.xyz + 3 * i + 2), X0, X1, X2);
       camera(cam, X0, X1, X2, u0, v0, zd);  // defined: the point passed a fuzzy test
       float tau[C];
       load_desc<C, TF>(feat, i, a.log_desc, tau);
-      pt[lane * PS + 0] = zd;
-      pt[lane * PS + 1] = u0;
-      pt[lane * PS + 2] = v0;
+      float* sp = pt + lane * PS;
+      sp[0] = zd;
+      sp[1] = u0;
+      sp[2] = v0;
+      sp[3] = X0;
+      sp[4] = X1;
+      sp[5] = X2;
 #pragma unroll
-      for (int k = 0; k < C; ++k) pt[lane * PS + 3 + k] = tau[k];
+      for (int k = 0; k < C; ++k) sp[6 + k] = tau[k];
     }
 #pragma unroll
     for (int k = 0; k < C + 2; ++k) acc[lane * AS + k] = 0.0f;
@@ -405,11 +408,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
     int slot = incl - cnt;
     for (uint32_t m = mask; m; m &= m - 1) item[slot++] = (uint8_t)((lane << 3) | (__ffs(m) - 1));
     __syncwarp();
-    for (int r = 0; r < total; r += 32) {
+    for (int r = 0; r < total; r += 32) {  // warp-uniform: every lane takes part in the shuffles
       const int k = r + lane;
+      // this lane's pair: dI/dtau = G/|Lambda| and the layer-0 pixel gradient
+      float v[C + 2];
+#pragma unroll
+      for (int c = 0; c < C + 2; ++c) v[c] = 0.0f;
+      int src = -1 - lane;  // lanes without a pair form runs of their own
       if (k < total) {
         const int it = item[k];
-        const int src = it >> 3, l = it & 7;
+        src = it >> 3;
+        const int l = it & 7;
         const float* sp = pt + src * PS;
         const float z = sp[0];
         int32_t pu, pv;
@@ -420,36 +429,78 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
           const float4 ip = ld_keep(info + gp, pol);
           float G[GS];
           load_keep<GS>(cam.gpm + gp * GS, G, pol);
-          float* ap = acc + src * AS;
 #pragma unroll
-          for (int c = 0; c < C; ++c) atomicAdd(ap + c, __fdiv_rn(G[c], ip.y));
+          for (int c = 0; c < C; ++c) v[c] = __fdiv_rn(G[c], ip.y);
           if (spatial_out) {
             float tau[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) tau[c] = sp[3 + c];
+            for (int c = 0; c < C; ++c) tau[c] = sp[6 + c];
             float g_u, g_v;
             spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, z, a.a1, tau, g_u, g_v, pol);
             const float sc = layer_scale(l);
-            atomicAdd(ap + C, g_u * sc);
-            atomicAdd(ap + C + 1, g_v * sc);
+            v[C] = g_u * sc;
+            v[C + 1] = g_v * sc;
           }
         }
       }
+      // A point's pairs are consecutive in the list: sum each run of equal
+      // src over the lanes (segmented reduction, run ends from a ballot), and
+      // let the run's first lane add it to the point's sums.  Runs are
+      // disjoint within a round and rounds follow each other, so plain adds
+      // suffice.
+      const int next = __shfl_down_sync(0xffffffffu, src, 1);
+      const int prev = __shfl_up_sync(0xffffffffu, src, 1);
+      const uint32_t tails = __ballot_sync(0xffffffffu, lane == 31 || next != src);
+      const int end = __ffs(tails & (0xffffffffu << lane)) - 1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int c = 0; c < C + 2; ++c) {
+          const float t = __shfl_down_sync(0xffffffffu, v[c], o);
+          if (lane + o <= end) v[c] += t;
+        }
+      }
+      if (src >= 0 && (lane == 0 || prev != src)) {
+        float* ap = acc + src * AS;
+#pragma unroll
+        for (int c = 0; c < C + 2; ++c) ap[c] += v[c];
+      }
     }
     __syncwarp();
+    float red[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) red[k] = 0.0f;
     if (i < a.n) {
+      const float* sp = pt + lane * PS;
       float gf[C];
 #pragma unroll
-      for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k] * (a.log_desc && mask ? pt[lane * PS + 3 + k] : 1.0f);
+      for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k] * (a.log_desc && mask ? sp[6 + k] : 1.0f);
       // (binned: the points in no Lambda were already given zero gradients)
       float gx[3] = {0.0f, 0.0f, 0.0f};
       const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];
-      if (mask && (du0 != 0.0f || dv0 != 0.0f)) chain_rule(cam, X0, X1, X2, du0, dv0, red, gx);
+      if (mask && (du0 != 0.0f || dv0 != 0.0f)) chain_rule(cam, sp[3], sp[4], sp[5], du0, dv0, red, gx);
       write_point_grads<C>(b, i, gf, gx, mask != 0u);
+    }
+    if (b.partials != nullptr) {  // this batch's pose / intrinsics terms into the warp's sums
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        float t = red[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == k) s_red[warp][k] += t;
+      }
     }
     __syncwarp();
   }
-  if (b.partials != nullptr) block_partials(b, red);
+  if (b.partials != nullptr) {
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      float t = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += s_red[w][threadIdx.x];
+      b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + threadIdx.x] = t;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
