@@ -207,6 +207,51 @@ def recorded_traffic(kernel: str):
     return d["dram_bytes_per_launch"] if h.hexdigest() == d["sources_sha1"] else None
 
 
+def recorded_atomics(kernel: str):
+    """L2 atomic requests per launch and the L2 atomic unit's busy fraction
+    for `kernel` from the same ncu summary, or None (as recorded_traffic)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d or "l2_atomic_requests_per_launch" not in d:
+        return None
+    h = hashlib.sha1()
+    for rel in d["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != d["sources_sha1"]:
+        return None
+    return d["l2_atomic_requests_per_launch"], d.get("l2_atomic_unit_active_pct")
+
+
+def atomic_peaks(device, px: int, ops: int = 1 << 26) -> dict:
+    """Random-address atomic throughput on buffers the size of the 1080p
+    pyramid's key, count and sum buffers (adop_atomic_probe, CUDA events,
+    best of 3): the ceiling for the depth and accumulate passes, in atomics
+    per second (one L2 request each, as the addresses are random)."""
+    import torch
+    import paper_2110_06635_gb300 as adop
+    out = {}
+    for name, kind, dt, elems, per in (("atomic_min_u64", 0, torch.int64, px, 1), ("atomic_add_u32", 1, torch.int32, px, 1),
+                                       ("atomic_add_f32x4", 2, torch.float32, 2 * px, 4)):
+        buf = torch.zeros(elems * per, dtype=dt, device=device)
+        adop.adop_atomic_probe(kind, buf, elems, ops, 7)
+        best = float("inf")
+        for r in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            adop.adop_atomic_probe(kind, buf, elems, ops, 11 + r)
+            b.record()
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[name] = round(ops / (best * 1e-3), 1)
+        del buf
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -672,6 +717,27 @@ def bench_serving(device, seconds: float = 10.0, rate: float = 200.0) -> dict:
     return out
 
 
+def atomic_roofline(device, wl, ks) -> dict:
+    """The second ceiling of the depth and accumulate passes: L2 atomics.
+    Achieved = L2 atomic requests per launch (ncu, committed summary) / the
+    launch's CUDA-event time; peak = the random-address probe's rate."""
+    peaks = atomic_peaks(device, wl.px)
+    out = {"unit": "L2 atomic requests/s", "peaks": peaks,
+           "l2_bytes": int(getattr(__import__("torch").cuda.get_device_properties(device), "L2_cache_size", 0)),
+           "pixel_state_bytes": wl.px * (8 + 4 + 4 * wl.c)}
+    for name, peak_key in (("depth", "atomic_min_u64"), ("accumulate", "atomic_add_f32x4")):
+        rec = recorded_atomics(name)
+        if rec is None or name not in ks:
+            out[name] = None
+            continue
+        req, busy = rec
+        t = ks[name][1] / ks[name][0] * 1e-3
+        out[name] = {"l2_atomic_requests_per_launch": req, "achieved": round(req / t, 1),
+                     "peak": peaks[peak_key], "frac": round(req / t / peaks[peak_key], 4),
+                     "l2_atomic_unit_active_pct_ncu": busy}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -707,6 +773,7 @@ def main():
                    "points_in_lambda": wl.n_vis,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
+        "atomic_roofline": None if args.profile_only else atomic_roofline(device, wl, ks),
         "kernel_ms": kernel_ms,
         "step_hbm_fraction": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
         "gpu_launches": int(sum(v[0] for v in ks.values())),

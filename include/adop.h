@@ -402,6 +402,19 @@ adop_status adop_point_radius(const float* xyz, int64_t n, int32_t k, float* rad
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* adop_last_error(void);
 
+/*
+ * Measurement aid, not part of the paper: launch `ops` atomics of one kind at
+ * uniformly random elements of buf (device, elems elements of the kind's
+ * size, elems < 2^32; hash of seed + op index): kind 0 = 64-bit unsigned
+ * atomicMin (the depth pass's key update), 1 = 32-bit integer add (|Lambda|),
+ * 2 = 16-byte float4 add (the accumulate pass's vector atomics), 3 = 32-bit
+ * float add.  The caller times the launch on `stream`; the result in buf is
+ * meaningless.  Used for the L2-atomic ceiling of the depth and accumulate
+ * passes.
+ */
+adop_status adop_atomic_probe(int32_t kind, void* buf, int64_t elems, int64_t ops, uint64_t seed,
+                              adop_stream stream);
+
 /* ADOP_ABI_VERSION of the loaded library. */
 int32_t adop_abi_version(void);
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "adop_env_backward": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32, _P, _P, _P, _P]),
     "adop_photometric_workspace_bytes": (ct.c_size_t, [ct.c_int32]),
     "adop_photometric_backward": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32, _P, _P, _P, _P, _P, ct.c_size_t, _P]),
+    "adop_atomic_probe": (ct.c_int, [ct.c_int32, _P, ct.c_int64, ct.c_int64, ct.c_uint64, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
     "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
 }
@@ -345,6 +346,11 @@ def adop_photometric_backward(cams, params: Params, c: int, frames, grad_image0,
     wp, wn = _ws_ptr(ws)
     _check(lib.adop_photometric_backward(arr, len(cams), ct.byref(pr), int(c), fr, g0, _dev_ptr(grad_photo),
                                          _dev_ptr(grad_crf), wp, wn, _stream_ptr(stream)))
+
+
+def adop_atomic_probe(kind: int, buf, elems: int, ops: int, seed: int = 0, stream=None):
+    """Launch `ops` random atomics of one kind into buf (measurement aid, see include/adop.h)."""
+    _check(load().adop_atomic_probe(int(kind), _dev_ptr(buf), int(elems), int(ops), int(seed), _stream_ptr(stream)))
 
 
 def adop_env_backward(cams, params: Params, c: int, frames, grad_images, grad_env, stream=None, crf_luts=None):
