@@ -452,8 +452,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       const int prev = __shfl_up_sync(0xffffffffu, src, 1);
       const uint32_t tails = __ballot_sync(0xffffffffu, lane == 31 || next != src);
       const int end = __ffs(tails & (0xffffffffu << lane)) - 1;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
+      // a run is at most `levels` long (one pair per layer); stop at the
+      // first step that no run needs
+      for (int o = 1; o < a.levels && __any_sync(0xffffffffu, lane + o <= end); o <<= 1) {
 #pragma unroll
         for (int c = 0; c < C + 2; ++c) {
           const float t = __shfl_down_sync(0xffffffffu, v[c], o);

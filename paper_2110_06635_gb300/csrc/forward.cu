@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
 // issued only if the point can still win (most points are occluded).
 // (Measured on GB300: grouping lanes that share a pixel with
 // __match_any_sync was 4x slower -- the per-group warp intrinsics serialise
-// -- and reading all layers' keys before the atomics was 15% slower.)
+// -- reading all layers' keys before the atomics was 15% slower, and
+// interleaving two points per thread 25% slower.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
       if (a.radius && !discard_keep(cam, zd, rw, bt, a.g2, l)) continue;
       if (!pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) continue;
       unsigned long long* slot = cam.key[l] + (int64_t)pv * (cam.w >> l) + pu;
-      if (key < __ldcg(slot)) atomicMin(slot, key);
+      // (an L1-cached read may be stale, but keys only decrease: a stale
+      // value can cost an atomic that loses, never skip one that wins)
+      if (key < __ldca(slot)) atomicMin(slot, key);
     }
   }
 }
