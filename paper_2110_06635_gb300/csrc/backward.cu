@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
   __shared__ float s_pt[kWarps][32 * PS];
   __shared__ float s_acc[kWarps][32 * AS];
   __shared__ uint8_t s_item[kWarps][32 * ADOP_MAX_LEVELS];
-  __shared__ float s_red[kWarps][12];
+  __shared__ float s_red[12][kThreads];  // per thread: its points' pose / intrinsics terms
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
   float* acc = s_acc[warp];
   uint8_t* item = s_item[warp];
   const uint64_t pol = policy_evict_last();
-  if (lane < 12) s_red[warp][lane] = 0.0f;  // pose / intrinsics sums of this warp
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s_red[k][threadIdx.x] = 0.0f;
 
   // the points to visit: all, in index order, or the visible ones tile by tile
   const int64_t count = BINNED ? (int64_t)cam.bin_off[cam.tiles] : a.n;
@@ -468,9 +469,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       }
     }
     __syncwarp();
-    float red[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) red[k] = 0.0f;
     if (i < a.n) {
       const float* sp = pt + lane * PS;
       float gf[C];
@@ -479,27 +477,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       // (binned: the points in no Lambda were already given zero gradients)
       float gx[3] = {0.0f, 0.0f, 0.0f};
       const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];
-      if (mask && (du0 != 0.0f || dv0 != 0.0f)) chain_rule(cam, sp[3], sp[4], sp[5], du0, dv0, red, gx);
-      write_point_grads<C>(b, i, gf, gx, mask != 0u);
-    }
-    if (b.partials != nullptr) {  // this batch's pose / intrinsics terms into the warp's sums
+      if (mask && (du0 != 0.0f || dv0 != 0.0f)) {
+        float red[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        float t = red[k];
+        for (int k = 0; k < 12; ++k) red[k] = s_red[k][threadIdx.x];
+        chain_rule(cam, sp[3], sp[4], sp[5], du0, dv0, red, gx);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == k) s_red[warp][k] += t;
+        for (int k = 0; k < 12; ++k) s_red[k][threadIdx.x] = red[k];
       }
+      write_point_grads<C>(b, i, gf, gx, mask != 0u);
     }
     __syncwarp();
   }
-  if (b.partials != nullptr) {
+  if (b.partials != nullptr) {  // block sum of the pose / intrinsics terms: warp w takes terms w, w + 8
     __syncthreads();
-    if (threadIdx.x < 12) {
+    for (int k = warp; k < 12; k += kWarps) {
       float t = 0.0f;
+      for (int j = lane; j < kThreads; j += 32) t += s_red[k][j];
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) t += s_red[w][threadIdx.x];
-      b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + threadIdx.x] = t;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + k] = t;
     }
   }
 }
