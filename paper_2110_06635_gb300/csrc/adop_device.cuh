@@ -135,6 +135,23 @@ __device__ __forceinline__ void load_keep(const float* __restrict__ src, float* 
   }
 }
 
+// load_keep for rows whose start is 32-byte aligned: 256-bit loads (sm_100+)
+// when N is a multiple of 8, so that a pixel's C = 8 gradient is one load.
+template <int N>
+__device__ __forceinline__ void load_keep_row(const float* __restrict__ src, float* dst, uint64_t pol) {
+  if constexpr (N % 8 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 8; ++v) {
+      float* d = dst + 8 * v;
+      asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+          : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7])
+          : "l"(src + 8 * v), "l"(pol));
+    }
+  } else {
+    load_keep<N>(src, dst, pol);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 projection contract
 // ---------------------------------------------------------------------------

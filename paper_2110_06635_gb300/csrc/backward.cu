@@ -249,7 +249,7 @@ __device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __
     else wgt = __frcp_rn(1.0f + iq[s].y);                        // joins the fuzzy blend
     if (wgt == 0.0f) continue;
     float G[GS];
-    load_keep<GS>(cam.gpm + gq[s] * GS, G, pol);
+    load_keep_row<GS>(cam.gpm + gq[s] * GS, G, pol);
     float dot = 0.0f;
 #pragma unroll
     for (int k = 0; k < C; ++k) dot = fmaf(G[k], tau[k], dot);
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
           const int64_t gp = lb + (int64_t)pv * wl + pu;
           const float4 ip = ld_keep(info + gp, pol);
           float G[GS];
-          load_keep<GS>(cam.gpm + gp * GS, G, pol);
+          load_keep_row<GS>(cam.gpm + gp * GS, G, pol);
 #pragma unroll
           for (int c = 0; c < C; ++c) v[c] = __fdiv_rn(G[c], ip.y);
           if (spatial_out) {
