@@ -121,6 +121,23 @@ __device__ __forceinline__ void store_vec(float* dst, const float* src) {
   }
 }
 
+// Store n floats to a 32-byte-aligned row: 256-bit stores when n is a
+// multiple of 8 (sm_100+), else as store_vec.
+template <int N>
+__device__ __forceinline__ void store_row(float* dst, const float* src) {
+  if constexpr (N % 8 == 0) {
+#pragma unroll
+    for (int v = 0; v < N / 8; ++v) {
+      const float* q = src + 8 * v;
+      asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                   :: "l"(dst + 8 * v), "f"(q[0]), "f"(q[1]), "f"(q[2]), "f"(q[3]), "f"(q[4]), "f"(q[5]), "f"(q[6]),
+                      "f"(q[7]) : "memory");
+    }
+  } else {
+    store_vec<N>(dst, src);
+  }
+}
+
 // load_vec with the L2 policy on every 16-byte piece (scalar pieces: plain loads).
 template <int N>
 __device__ __forceinline__ void load_keep(const float* __restrict__ src, float* dst, uint64_t pol) {

@@ -46,13 +46,13 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     if (n == 0 && !a.env) {
 #pragma unroll
       for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
-    } else if (n == 0) {  // the environment map's value, kept in acc by k_env_fill
+    } else {  // (an empty pixel's acc holds the environment map's value, kept by k_env_fill)
+      load_vec<C>(cam.acc + g * C, I);
+      if (n != 0) {
+        const float fn = (float)n;
 #pragma unroll
-      for (int k = 0; k < C; ++k) I[k] = cam.acc[g * C + k];
-    } else {
-      const float fn = (float)n;
-#pragma unroll
-      for (int k = 0; k < C; ++k) I[k] = __fdiv_rn(cam.acc[g * C + k], fn);
+        for (int k = 0; k < C; ++k) I[k] = __fdiv_rn(I[k], fn);
+      }
     }
     const float* gl = cam.grad[l];
 #pragma unroll
@@ -73,15 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     for (int k = 0; k < C; ++k) gi = fmaf(G[k], I[k], gi);
     reinterpret_cast<float4*>(cam.info)[g] =
         make_float4(__uint_as_float((uint32_t)(key >> 32)), (float)n, gi, 0.0f);
-    float* dst = cam.gpm + g * GS;
-    if constexpr (GS % 4 == 0) {
-#pragma unroll
-      for (int v = 0; v < GS / 4; ++v)
-        reinterpret_cast<float4*>(dst)[v] = make_float4(G[4 * v], G[4 * v + 1], G[4 * v + 2], G[4 * v + 3]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < GS; ++k) dst[k] = G[k];
-    }
+    store_row<GS>(cam.gpm + g * GS, G);  // (rows of GS floats in a 256-byte-aligned workspace block)
   }
 }
 
