@@ -40,23 +40,22 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const int l = layer_of(cam, a.levels, g);
     const int64_t p = g - cam.off[l];
     const int64_t np = cam.off[l + 1] - cam.off[l];
+    // every load up front, independent of the count: one round trip per pixel
     const uint32_t n = cam.cnt[l][p];
     const unsigned long long key = cam.key[l][p];
     float I[C], G[GS];
-    if (n == 0 && !a.env) {
-#pragma unroll
-      for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
-    } else {  // (an empty pixel's acc holds the environment map's value, kept by k_env_fill)
-      load_vec<C>(cam.acc + g * C, I);
-      if (n != 0) {
-        const float fn = (float)n;
-#pragma unroll
-        for (int k = 0; k < C; ++k) I[k] = __fdiv_rn(I[k], fn);
-      }
-    }
+    load_vec<C>(cam.acc + g * C, I);
     const float* gl = cam.grad[l];
 #pragma unroll
     for (int k = 0; k < C; ++k) G[k] = gl ? __ldg(gl + k * np + p) : 0.0f;
+    if (n == 0 && !a.env) {
+#pragma unroll
+      for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
+    } else if (n != 0) {  // (an empty pixel's acc holds the environment map's value, kept by k_env_fill)
+      const float fn = (float)n;
+#pragma unroll
+      for (int k = 0; k < C; ++k) I[k] = __fdiv_rn(I[k], fn);
+    }
 #pragma unroll
     for (int k = C; k < GS; ++k) G[k] = 0.0f;
     if (l == 0 && cam.epi) {

@@ -157,28 +157,18 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ 
     if (img == nullptr) continue;
     const int64_t p = g - cam.off[l];
     const int64_t np = cam.off[l + 1] - cam.off[l];
+    // the count and the sums are loaded together: one round trip per pixel
     const uint32_t n = cam.cnt[l][p];
     float v[C];
+    load_vec<C>(cam.acc + g * C, v);
     if (n == 0) {
       if (a.env) continue;  // the environment map's pixels: k_env_fill
 #pragma unroll
       for (int k = 0; k < C; ++k) v[k] = a.background ? __ldg(a.background + k) : 0.0f;
     } else {
-      const float* acc = cam.acc + g * C;
       const float fn = (float)n;
-      if constexpr (C % 4 == 0) {
 #pragma unroll
-        for (int q = 0; q < C / 4; ++q) {
-          const float4 s = reinterpret_cast<const float4*>(acc)[q];
-          v[4 * q] = __fdiv_rn(s.x, fn);
-          v[4 * q + 1] = __fdiv_rn(s.y, fn);
-          v[4 * q + 2] = __fdiv_rn(s.z, fn);
-          v[4 * q + 3] = __fdiv_rn(s.w, fn);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < C; ++k) v[k] = __fdiv_rn(acc[k], fn);
-      }
+      for (int k = 0; k < C; ++k) v[k] = __fdiv_rn(v[k], fn);
     }
     if (l == 0 && cam.epi) {
       const int32_t pu = (int32_t)(p % cam.w), pv = (int32_t)(p / cam.w);
