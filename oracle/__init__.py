@@ -247,6 +247,29 @@ def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, n
     return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)
 
 
+def keys_counts(xyz, cam, levels=4, alpha=0.01, znear=1e-3) -> Forward:
+    """Sec. 3.1's forward without descriptors: every point's pixel per layer
+    and depth (Eq. render ... Eq. boundscheck), the nearest-depth keys and the
+    fuzzy-test counts |Lambda| (Eq. depthtest) -- for clouds too large to
+    blend in FP64 here.  ``img`` is empty."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    n = xyz.shape[0]
+    npx = int(lib.orc_pyramid_pixels(int(cam.w), int(cam.h), int(levels)))
+    keys = np.empty(npx, dtype=np.uint64)
+    cnt = np.empty(npx, dtype=np.uint32)
+    img = np.empty(1, dtype=np.float64)
+    pix = np.empty((n, levels), dtype=np.int32)
+    z = np.empty(n, dtype=np.float32)
+    K, T = _intr(cam), _pose(cam)
+    rc = lib.orc_forward(n, _ptr(xyz), 0, None, None, ct.byref(K), ct.byref(T), int(levels), ct.c_float(alpha),
+                         ct.c_float(znear), None, None, None, ct.c_float(1.5), 0, None, 0, 0,
+                         _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
+    if rc != 0:
+        raise MemoryError("oracle forward: allocation failed")
+    return Forward(keys, cnt, img[:0], pix, z, int(cam.w), int(cam.h), int(levels), 0)
+
+
 def camera_inverse(cam, u0, v0):
     """Unit camera-space direction of the ray through layer-0 coordinates (u0, v0)."""
     lib = _load()

@@ -169,6 +169,45 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
     return res
 
 
+# |x - boundary| below which the GPU's FP32 and the oracle's FP64 response
+# input x may fall on different sides of a response-curve knot or of the ends
+# of [0, 1] (x carries the FP32 error of the blended mean, ~1e-6 absolute)
+EPI_AMBIGUOUS = 1e-5
+
+
+def epilogue_decidable_grads(orc, scene, cams, grads, dtype="f32", levels=4, leaky=False, env=None):
+    """The upstream gradients with layer 0's channels 0..2 zeroed where the
+    photometric response's input x lies within EPI_AMBIGUOUS of a knot of the
+    LUT or of 0 or 1.  The response's slope jumps there, so which slope
+    chains the gradient is decided by the last bits of x, and both slopes are
+    correct answers; zeroing G there (on both sides) compares only what is
+    unique.  Uses the oracle's forward for x."""
+    out = []
+    for k, cam in enumerate(cams):
+        G = [np.array(g, np.float64, copy=True) for g in grads[k]]
+        crf = getattr(cam, "crf", None)
+        if getattr(cam, "epilogue", False) and crf is not None:
+            f = orc.forward(scene.xyz, scene.feat_as(dtype), cam, levels,
+                            env=None if env is None else np.asarray(env, np.float64))
+            c, h, w = scene.c, cam.h, cam.w
+            I = f.img[:c * h * w].reshape(c, h, w)
+            blended = f.cnt[:h * w].reshape(h, w) > 0  # empty pixels hold the same constant on both sides
+            v, u = np.mgrid[0:h, 0:w]
+            r2 = (u / w - cam.vig_c[0]) ** 2 + (v / h - cam.vig_c[1]) ** 2
+            a = cam.vig_a
+            vig = 1.0 + r2 * (a[0] + r2 * (a[1] + r2 * a[2]))
+            n1 = np.asarray(crf).shape[-1] - 1
+            for ch in range(min(c, 3)):
+                x = I[ch] * 2.0 ** -cam.ev * cam.wb[ch] * vig
+                t = np.clip(x, 0.0, 1.0) * n1
+                near_knot = (np.abs(t - np.round(t)) / n1 < EPI_AMBIGUOUS) & (x > -EPI_AMBIGUOUS) & \
+                    (x < 1.0 + EPI_AMBIGUOUS)
+                near_end = (np.abs(x) < EPI_AMBIGUOUS) | (np.abs(x - 1.0) < EPI_AMBIGUOUS)
+                G[0][ch][(near_knot | near_end) & blended] = 0.0
+        out.append(G)
+    return out
+
+
 def compare(gpu, ref, dtype="f32", out_dtype="f32", check_state=True, backward=True, env=False):
     """Assert parity of every output; returns the measured relative errors."""
     errs = {}

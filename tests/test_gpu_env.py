@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import RTOL_ENV_GRAD, RTOL_ENV_IMG, RTOL_FEAT_F32, assert_close, compare, gpu_run, oracle_run
+from parity import (RTOL_ENV_GRAD, RTOL_ENV_IMG, RTOL_FEAT_F32, assert_close, compare, epilogue_decidable_grads,
+                    gpu_run, oracle_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +69,7 @@ def test_env_with_photometric_epilogue(adop, orc):
     cams = _cams()
     env = scenes.env_map(4, 64, 128, seed=89)
     G = [scenes.upstream_grad(c.w, c.h, 4, 4, 90 + k) for k, c in enumerate(cams)]
+    G = epilogue_decidable_grads(orc, sc, cams, G, env=env)
     g = gpu_run(adop, sc, cams, "f32", grads=G, env=env, flags=adop.ADOP_FLAG_EPILOGUE)
     r = oracle_run(orc, sc, cams, "f32", grads=G, env=env, epilogue=True)
     compare(g, r, env=True)

@@ -1,0 +1,133 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times.
+
+* Single view (5M points, 1920x1080, C = 8, kept state, per-point layer
+  masks, gradients assigned): the whole forward and backward against the
+  FP64 oracle, BF16 and FP32 descriptors.
+* Training step (20M points, 16 cameras of mixed resolution, BF16, photometric
+  epilogue, all cameras in one call): camera 0 against the oracle (forward
+  and backward of that camera), and the one-call backward of all 16 cameras
+  against the sum of 16 one-camera calls -- a property that holds at any size.
+* Large scene (120M points, C = 4 FP16, forward): keys and counts of a
+  1920x1080 and a 3840x2160 view bit-exact against the oracle's
+  descriptor-free forward, and the image at sampled pixels against the mean
+  of the descriptors of the points the oracle puts in Lambda there.
+"""
+import numpy as np
+import pytest
+
+import scenes
+from parity import (RTOL_FEAT_F32, RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run,
+                    rel_err)
+
+pytestmark = pytest.mark.gpu
+
+LEVELS = 4
+
+
+@pytest.fixture(scope="module")
+def single_view():
+    return scenes.config(2)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_single_view_full_size(adop, orc, single_view, dtype):
+    sc, cams = single_view
+    G = [scenes.upstream_grad(c.w, c.h, LEVELS, sc.c, 2024) for c in cams]
+    g = gpu_run(adop, sc, cams, dtype, grads=G, out_dtype=dtype, grad_assign=True)
+    r = oracle_run(orc, sc, cams, dtype, grads=G)
+    errs = compare(g, r, dtype, out_dtype=dtype)
+    # the workload is what the benchmark claims: most points occluded, a
+    # deep fuzzy-blend population
+    assert 1_000_000 < np.count_nonzero(g["cnt"][0]) and errs["dxyz"] <= RTOL_GRAD
+
+
+@pytest.fixture(scope="module")
+def training_scene():
+    return scenes.config(3)
+
+
+def test_training_step_views(adop, orc, training_scene):
+    sc, cams = training_scene
+    flags = adop.ADOP_FLAG_EPILOGUE
+    G = [scenes.upstream_grad(c.w, c.h, LEVELS, sc.c, 3000 + k) for k, c in enumerate(cams)]
+    G[:1] = epilogue_decidable_grads(orc, sc, cams[:1], G[:1], "bf16")  # camera 0 meets the oracle
+    g_all = gpu_run(adop, sc, cams, "bf16", grads=G, flags=flags)
+    # camera 0 through the oracle: forward and backward of that view
+    g0 = gpu_run(adop, sc, cams[:1], "bf16", grads=G[:1], flags=flags)
+    r0 = oracle_run(orc, sc, cams[:1], "bf16", grads=G[:1], epilogue=True)
+    compare(g0, r0, "bf16")
+    assert np.array_equal(g_all["keys"][0], r0["keys"][0]) and np.array_equal(g_all["cnt"][0], r0["cnt"][0])
+    assert_close(g_all["img"][0], r0["img"][0], RTOL_FEAT_F32, "camera 0 image in the 16-camera call")
+    # all 16 in one call (vector atomics across cameras) = the sum of the views
+    dfeat = np.zeros_like(g_all["dfeat"])
+    dxyz = np.zeros_like(g_all["dxyz"])
+    pose, intr = [], []
+    for k in range(len(cams)):
+        gk = g0 if k == 0 else gpu_run(adop, sc, cams[k:k + 1], "bf16", grads=G[k:k + 1], flags=flags)
+        assert np.array_equal(gk["keys"][0], g_all["keys"][k]), k
+        dfeat += gk["dfeat"]
+        dxyz += gk["dxyz"]
+        pose.append(gk["dpose"][0])
+        intr.append(gk["dintr"][0])
+    assert_close(g_all["dfeat"], dfeat, RTOL_GRAD, "dL/dtau, 16 cameras")
+    assert_close(g_all["dxyz"], dxyz, RTOL_GRAD, "dL/dx, 16 cameras")
+    assert_close(g_all["dpose"], np.array(pose), RTOL_GRAD, "pose gradients")
+    assert_close(g_all["dintr"], np.array(intr), RTOL_GRAD, "intrinsics gradients")
+
+
+@pytest.fixture(scope="module")
+def large_scene():
+    sc, _ = scenes.config(4)
+    return sc
+
+
+def _fp16_tensor(scene):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(scene.feat.astype(np.float16))).cuda()
+
+
+@pytest.mark.parametrize("res", [(1920, 1080), (3840, 2160)], ids=["1080p", "4k"])
+def test_large_scene_forward(adop, orc, large_scene, res):
+    import torch
+    sc = large_scene
+    cam = scenes.path_cameras(60, *res, seed=1004)[0]
+    pts = adop.Points(torch.from_numpy(sc.xyz).cuda(), _fp16_tensor(sc))
+    params = adop.Params(LEVELS, 0.01, 1e-3, None, 0)
+    fr = adop.Frame.alloc(cam, sc.c, LEVELS, torch.float32, True, "cuda")
+    ws = adop.alloc_workspace(pts, [cam], params, None, "cuda")
+    adop.adop_render_forward(pts, [cam], params, [fr], ws)
+    torch.cuda.synchronize()
+    keys = fr.key.cpu().numpy().view(np.uint64)
+    cnt = fr.count.cpu().numpy().view(np.uint32)
+    imgs = [im.cpu().numpy() for im in fr.images]
+    del pts, fr, ws
+    torch.cuda.empty_cache()
+    r = orc.keys_counts(sc.xyz, cam, LEVELS)
+    assert np.array_equal(keys, r.keys), f"{np.count_nonzero(keys != r.keys)} keys differ"
+    assert np.array_equal(cnt, r.cnt)
+    assert np.count_nonzero(cnt) > 0.5 * cnt.size
+    # sampled pixels of every layer: the mean over the points the oracle puts
+    # in Lambda (z <= f32(z_min * f32(1 + alpha))), in FP64
+    rng = np.random.default_rng(77)
+    a1 = np.float32(1.0) + np.float32(0.01)
+    off = 0
+    for l in range(LEVELS):
+        wl, hl = cam.w >> l, cam.h >> l
+        lk = r.keys[off:off + wl * hl]
+        hit = np.flatnonzero(r.cnt[off:off + wl * hl])
+        sample = np.sort(rng.choice(hit, min(400, hit.size), replace=False))
+        pl = r.pix[:, l]
+        sel = np.flatnonzero(np.isin(pl, sample))
+        zmin = (lk[pl[sel]] >> np.uint64(32)).astype(np.uint32).view(np.float32)
+        inl = sel[r.z[sel] <= zmin * a1]
+        ref = np.zeros((sample.size, sc.c))
+        n = np.zeros(sample.size)
+        idx = np.searchsorted(sample, pl[inl])
+        np.add.at(ref, idx, sc.feat[inl].astype(np.float16).astype(np.float64))
+        np.add.at(n, idx, 1.0)
+        assert np.array_equal(n, r.cnt[off + sample])
+        ref /= n[:, None]
+        got = imgs[l].reshape(sc.c, -1)[:, sample].T
+        assert rel_err(got, ref) <= RTOL_FEAT_F32, (l, rel_err(got, ref))
+        off += wl * hl

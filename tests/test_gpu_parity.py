@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import compare, gpu_run, oracle_run
+from parity import compare, epilogue_decidable_grads, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -121,7 +121,7 @@ def test_photometric_epilogue(adop, orc):
         R, t = scenes.look_at(-cam.R.T @ cam.t, np.full(3, 0.5))
         cam.R, cam.t = R, t
     sc.feat = np.abs(sc.feat) * 0.5  # radiance-like descriptors
-    G = _grads(cams, sc.c, 4, 53)
+    G = epilogue_decidable_grads(orc, sc, cams, _grads(cams, sc.c, 4, 53))
     g = gpu_run(adop, sc, cams, "f32", grads=G, flags=adop.ADOP_FLAG_EPILOGUE)
     r = oracle_run(orc, sc, cams, "f32", grads=G, epilogue=True)
     compare(g, r)

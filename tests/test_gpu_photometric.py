@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import RTOL_GRAD, assert_close, assert_reduced, compare, gpu_run, oracle_run
+from parity import RTOL_GRAD, assert_close, assert_reduced, compare, epilogue_decidable_grads, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +30,7 @@ def _scene():
 def test_leaky_epilogue_fwd_bwd(adop, orc, leaky):
     sc, cams = _scene(), _cams()
     G = [scenes.upstream_grad(c.w, c.h, 4, 4, 60 + k) for k, c in enumerate(cams)]
+    G = epilogue_decidable_grads(orc, sc, cams, G, leaky=leaky)
     flags = adop.ADOP_FLAG_EPILOGUE | (adop.ADOP_FLAG_LEAKY_CRF if leaky else 0)
     g = gpu_run(adop, sc, cams, "f32", grads=G, flags=flags)
     r = oracle_run(orc, sc, cams, "f32", grads=G, epilogue=True, leaky=leaky)

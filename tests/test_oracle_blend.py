@@ -270,3 +270,15 @@ def test_log_descriptors(orc):
             tm[i, ch] -= 1e-6
             fd = (G @ orc.forward(sc.xyz, tp, cam, log_desc=True).img - G @ orc.forward(sc.xyz, tm, cam, log_desc=True).img) / 2e-6
             assert np.isclose(fd, ga.dfeat[i, ch], rtol=1e-5, atol=1e-7)
+
+
+def test_keys_counts_equal_the_full_forward(orc):
+    # the descriptor-free forward used for the largest clouds is the same
+    # computation as the full forward, up to the blend
+    sc = tiny_spheres(4000, 4, seed=71)
+    cam = Camera(96, 64, 80.0, 80.0, 48.0, 32.0, k1=0.02, R=np.eye(3, dtype=np.float32),
+                 t=np.array([-0.5, -0.4, 2.5], np.float32))
+    f = orc.forward(sc.xyz, sc.feat, cam)
+    k = orc.keys_counts(sc.xyz, cam)
+    assert np.array_equal(f.keys, k.keys) and np.array_equal(f.cnt, k.cnt)
+    assert np.array_equal(f.pix, k.pix) and np.array_equal(f.z, k.z)
