@@ -164,3 +164,56 @@ def test_jacobians_match_finite_differences(orc, model):
             km[k] -= h
             fd = (cam_f64(kp, X) - cam_f64(km, X)) / (2 * h)
             assert np.allclose(fd, JK[:, k], rtol=1e-6, atol=1e-7 * max(1.0, np.abs(JK[:, k]).max()))
+
+
+def _nearest(pix, depth):
+    """pixel -> index of its nearest point (ties to the smaller index)."""
+    sel = np.flatnonzero(pix >= 0)
+    order = np.lexsort((sel, depth[sel], pix[sel]))
+    p = pix[sel][order]
+    first = np.r_[True, p[1:] != p[:-1]]
+    return dict(zip(p[first].tolist(), sel[order][first].tolist()))
+
+
+@pytest.mark.parametrize("which", ["tiny", "single_view_subsample"])
+def test_fp64_projection_statistic(orc, which):
+    """A statistic, not a gate: how often the FP32 projection contract puts a
+    (point, layer) pair in another pixel, or another point in front at a
+    pixel, than an FP64 projection of the same inputs would.  Both are rare
+    (the points within an FP32 rounding of a pixel edge or of a depth tie)."""
+    import scenes
+    if which == "tiny":
+        sc, cams = scenes.config(1)
+    else:
+        sc, cams = scenes.config(2, n=200_000)
+    cam = cams[0]
+    levels = 4
+    f = orc.keys_counts(sc.xyz, cam, levels)
+    R, t = cam.R.astype(np.float64), cam.t.astype(np.float64)
+    X = sc.xyz.astype(np.float64) @ R.T + t
+    k9 = np.array([np.float64(np.float32(getattr(cam, k))) for k in ("fx", "fy", "cx", "cy", "k1", "k2", "k3", "p1", "p2")])
+    uv = orc.camera_f64_many(k9, X, 0)
+    z = X[:, 2]
+    moved = 0
+    pairs = 0
+    winners_differ = 0
+    pixels = 0
+    for l in range(levels):
+        wl, hl = cam.w >> l, cam.h >> l
+        pu = np.rint(uv[:, 0] / 2 ** l)
+        pv = np.rint(uv[:, 1] / 2 ** l)
+        ok = (z > 1e-3) & (pu >= 0) & (pu < wl) & (pv >= 0) & (pv < hl)
+        p64 = np.where(ok, pv * wl + pu, -1).astype(np.int64)
+        p32 = f.pix[:, l].astype(np.int64)
+        both = (p32 >= 0) | (p64 >= 0)
+        pairs += int(both.sum())
+        moved += int((p32 != p64)[both].sum())
+        w32 = _nearest(p32, f.z.astype(np.float64))
+        w64 = _nearest(p64, z)
+        common = set(w32) & set(w64)
+        pixels += len(common)
+        winners_differ += sum(1 for p in common if w32[p] != w64[p])
+    frac_moved = moved / max(pairs, 1)
+    frac_winner = winners_differ / max(pixels, 1)
+    print(f"\n{which}: pairs in another pixel {frac_moved:.2e}, pixels with another nearest point {frac_winner:.2e}")
+    assert frac_moved < 1e-3 and frac_winner < 1e-3
