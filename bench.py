@@ -471,33 +471,30 @@ def bench_env(device, steps: int, warmup: int, flush) -> dict:
 
 
 def e2e_measure(wl, steps: int, warmup: int, device):
-    """Same step through the public API, from and to pinned host memory:
-    H2D of positions, descriptors and upstream gradients, D2H of the images
-    and all gradients, inside the timed region."""
-    import ctypes as ct
+    """The same step through the public API from and to pinned host memory
+    (paper_2110_06635_gb300.pipeline): every step copies its positions,
+    descriptors and upstream gradients host -> device and its images and all
+    gradients device -> host; the copies of neighbouring steps overlap the
+    kernels on separate streams.  Timed with CUDA events from before the first
+    copy to after the last."""
     import torch
-    pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)  # noqa: E731
-    h_in = [(pin(t), t) for t in (wl.xyz, wl.feat, *wl.G)]
-    for h, d in h_in:
-        h.copy_(d.cpu())
-    outs = [*wl.frame.images, wl.gfeat, wl.gxyz, wl.gpose, wl.gintr]
-    h_out = [(pin(t), t) for t in outs]
-    stream = torch.cuda.current_stream()
-    sp = ct.c_void_p(stream.cuda_stream)
-
-    def step():
-        for h, d in h_in:
-            d.copy_(h, non_blocking=True)
-        wl.step(sp)
-        for h, d in h_out:
-            h.copy_(d, non_blocking=True)
-
-    for _ in range(warmup):
-        step()
-    total_ms, _ = timed_steps(step, steps, None, None, device)
-    bi = sum(h.numel() * h.element_size() for h, _ in h_in)
-    bo = sum(h.numel() * h.element_size() for h, _ in h_out)
-    return total_ms, bi, bo
+    from paper_2110_06635_gb300.pipeline import HostPipeline, StepIO
+    pipe = HostPipeline(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS, device=device)
+    ios = [StepIO.alloc(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS) for _ in range(2)]
+    for io in ios:  # two host input sets, used alternately (each step still moves its own bytes)
+        io.xyz.copy_(wl.xyz.cpu())
+        io.feat.copy_(wl.feat.cpu())
+        for h, d in zip(io.grads, wl.G):
+            h.copy_(d.cpu())
+    pipe.run([ios[k % 2] for k in range(warmup)])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pipe.run([ios[k % 2] for k in range(steps)], start=a, end=b)
+    b.synchronize()
+    total_ms = a.elapsed_time(b)
+    del pipe
+    return total_ms, ios[0].bytes_in(), ios[0].bytes_out()
 
 
 def cpu_baseline(budget_s: float = 15.0):
