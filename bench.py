@@ -559,10 +559,23 @@ def bench_training_step(device, steps: int = 5, warmup: int = 3) -> dict:
     ks = adop.adop_profile_collect()
     adop.adop_profile_enable(False)
     views = len(cams)
+
+    # the alternative design: one camera per call (owner-computes gradients,
+    # no atomics across cameras), the cameras one after another
+    def step_by_camera():
+        for k in range(views):
+            imgs = rasterize(xyz, feat, cams[k:k + 1], xi[k:k + 1], levels=LEVELS, flags=adop.ADOP_FLAG_EPILOGUE,
+                             out_dtype=torch.bfloat16, keep_state=False, crf_luts=luts[k:k + 1])
+            torch.autograd.backward(imgs[0], G[k])
+
+    for _ in range(2):
+        step_by_camera()
+    seq_ms, _ = timed_steps(step_by_camera, steps, None, None, device)
     px = sum(adop.pyramid_offsets(c.w, c.h, LEVELS)[-1] for c in cams)
     out = {"workload": f"{sc.n} points C=8 BF16, {views} cameras 960x540..1920x1080 ({px} pyramid px), "
                        "fwd+bwd via autograd, epilogue on, depth re-rendered in backward",
            "ms_per_step": round(total_ms / steps, 3),
+           "ms_per_step_camera_by_camera": round(seq_ms / steps, 3),
            "point_views_per_s": round(sc.n * views * steps / (total_ms / 1e3), 1),
            "gpu_launches_per_step": round(sum(v[0] for v in ks.values()) / steps, 2),
            "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in ks.items()}}

@@ -250,6 +250,16 @@ __device__ __forceinline__ bool pixel_at(float u0, float v0, int l, int32_t w, i
   return pu >= 0 && pu < wl && pv >= 0 && pv < hl;
 }
 
+// One test for all layers: false when (u0, v0) is out of bounds at every
+// layer l < levels (u0 <= -2^(levels-1) or u0 >= w + 2^(levels-1) puts
+// u0 2^-l outside ]-1, w_l + 1[ for each such l; likewise v), so pixel_at
+// need not run four times for the many points outside the view.  Exact:
+// it never rejects a point that some layer keeps.
+__device__ __forceinline__ bool in_pyramid(float u0, float v0, int32_t w, int32_t h, int levels) {
+  const float m = (float)(1 << (levels - 1));
+  return u0 > -m && u0 < (float)w + m && v0 > -m && v0 < (float)h + m;
+}
+
 // Eq. discard (stochastic point discarding): keep the point at layer l iff
 // (t * t) * g2 > 1 - beta, t = (f32(fx 2^-l) * r_world) / z, g2 = f32(gamma^2):
 // the paper's r_screen / sqrt(1 - beta) > 1 / gamma without the square root,

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
     float X0, X1, X2, u0, v0, zd;
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
     if (!camera(cam, X0, X1, X2, u0, v0, zd) || !(zd > a.znear)) continue;
+    if (!in_pyramid(u0, v0, cam.w, cam.h, a.levels)) continue;
     if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
     const unsigned long long key = depth_key(zd, i);
     const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
     uint32_t mask = 0;  // bit l: the point is in Lambda of its layer-l pixel
     float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd;
     transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
-    if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) &&
+    if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) && in_pyramid(u0, v0, cam.w, cam.h, a.levels) &&
         !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
       const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
       int64_t pix[kL];
