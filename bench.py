@@ -277,8 +277,9 @@ def algorithmic_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: 
         "accumulate": n * (12 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
         "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
-        "bwd_bin": n * 8 + nv * 4 + (n - nv) * (4 * c + 12),          # masks twice -> list; zero grads
-        "bwd_points": nv * (4 + 4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs),  # list, mask, xyz, tau -> grads
+        "bwd_bin": n * 8 + nv * 4,                                    # masks twice -> list
+        # list, mask, xyz, tau -> grads of the visible points; pixel records; masks -> zero grads of the rest
+        "bwd_points": nv * (4 + 4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs) + n * 4 + (n - nv) * (4 * c + 12),
         "bwd_reduce": 0,
     }[kernel]
 

@@ -21,7 +21,7 @@
 //                  visible points are visited 32x32-pixel screen tile by
 //                  tile, so the pixel records a warp reads stay in cache.
 //   k_bin_*        count the visible points per screen tile, scan, scatter
-//                  their indices tile by tile (and zero the others' gradients).
+//                  their indices tile by tile.
 //   k_bwd_reduce   sums the block partials in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       float gf[C];
 #pragma unroll
       for (int k = 0; k < C; ++k) gf[k] = acc[lane * AS + k] * (a.log_desc && mask ? sp[6 + k] : 1.0f);
-      // (binned: the points in no Lambda were already given zero gradients)
+      // (binned: the points in no Lambda get zero gradients after the loop)
       float gx[3] = {0.0f, 0.0f, 0.0f};
       const float du0 = acc[lane * AS + C], dv0 = acc[lane * AS + C + 1];
       if (mask && (du0 != 0.0f || dv0 != 0.0f)) {
@@ -479,6 +479,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       write_point_grads<C>(b, i, gf, gx, mask != 0u);
     }
     __syncwarp();
+  }
+  if (BINNED && b.mode == kGradAssign) {
+    // the points in no Lambda get zero gradients here: streaming stores that
+    // overlap the blocks still busy with latency-bound pairs (in the binning
+    // kernel they cost 34 us, here 24)
+    const float zf[C] = {};
+    const float zx[3] = {0.0f, 0.0f, 0.0f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+      if ((__ldcs(cam.vis + i) & 0xFFu) == 0u) write_point_grads<C>(b, i, zf, zx, false);
   }
   if (b.partials != nullptr) {  // block sum of the pose / intrinsics terms: warp w takes terms w, w + 8
     __syncthreads();
@@ -582,13 +591,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(const __grid_constant_
     int32_t slot = 0;
     if (active && rank == 0) slot = atomicAdd(cam.bin_count + tile, len);
     slot = __shfl_sync(0xffffffffu, slot, head) + rank;
-    if (active) {
-      cam.bin_list[slot] = (int32_t)i;
-    } else if (i < a.n && b.mode == kGradAssign) {
-      const float zf[C] = {};
-      const float zx[3] = {0.0f, 0.0f, 0.0f};
-      write_point_grads<C>(b, i, zf, zx, false);
-    }
+    if (active) cam.bin_list[slot] = (int32_t)i;
   }
 }
 
@@ -647,13 +650,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_const
   __syncthreads();
   for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     const uint32_t v = __ldg(cam.vis + i);
-    if (v & 0xFFu) {
-      cam.bin_list[atomicAdd(bins + min(v >> 8, (uint32_t)T - 1u), 1)] = (int32_t)i;
-    } else if (b.mode == kGradAssign) {
-      const float zf[C] = {};
-      const float zx[3] = {0.0f, 0.0f, 0.0f};
-      write_point_grads<C>(b, i, zf, zx, false);
-    }
+    if (v & 0xFFu) cam.bin_list[atomicAdd(bins + min(v >> 8, (uint32_t)T - 1u), 1)] = (int32_t)i;
   }
 }
 

@@ -51,8 +51,8 @@ cudaError_t launch_bwd_prepass(const LaunchCams& cams, const PointArgs& a, int c
 cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c,
                               adop_dtype fd, int blocks_x, cudaStream_t s);
 // Screen-tile binning of the visible points (backward): count, scan, scatter.
-// Also writes zero gradients of the points that are in no Lambda when the
-// mode is kGradAssign.
+// (The binned point pass then also writes the zero gradients of the points
+// that are in no Lambda when the mode is kGradAssign.)
 cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c, cudaStream_t s);
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s);

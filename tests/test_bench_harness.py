@@ -55,7 +55,8 @@ def test_algorithmic_bytes_model():
     n, px, c = 1000, 500, 8
     assert bench.algorithmic_bytes("depth", n, px, c, 2, 2) == n * 12 + px * 16
     # the backward point pass reads and writes only the points in some Lambda
-    assert bench.algorithmic_bytes("bwd_points", n, px, c, 2, 2, 400) == 400 * (4 + 4 + 12 + 16 + 32 + 12) + px * 48
-    assert bench.algorithmic_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4 + 600 * (32 + 12)
+    assert bench.algorithmic_bytes("bwd_points", n, px, c, 2, 2, 400) == \
+        400 * (4 + 4 + 12 + 16 + 32 + 12) + px * 48 + n * 4 + 600 * (32 + 12)
+    assert bench.algorithmic_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
     with pytest.raises(KeyError):
         bench.algorithmic_bytes("nope", n, px, c, 2, 2)
