@@ -1,0 +1,64 @@
+"""The C ABI under CUDA graph capture: a forward + backward step captured once
+and replayed gives the results of the same step run eagerly (the library
+launches only on the caller's stream, allocates nothing and synchronises
+nothing inside a call, so its launches can be captured)."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import scenes
+from parity import RTOL_FEAT_F32, RTOL_GRAD, assert_close, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def test_captured_step_equals_eager_step(adop):
+    import torch
+    from paper_2110_06635_gb300 import _abi as A
+    sc, cams = scenes.config(1)
+    cam = cams[0]
+    G = scenes.upstream_grad(cam.w, cam.h, 4, sc.c, 41)
+    ref = gpu_run(adop, sc, [cam], "f32", grads=[G], grad_assign=True)
+    dev = "cuda"
+    pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+    params = adop.Params(4, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+    fr = adop.Frame.alloc(cam, sc.c, 4, torch.float32, True, dev, sc.n)
+    ws = adop.alloc_workspace(pts, [cam], params, None, dev)
+    gimg = [torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in G]
+    gfeat = torch.empty((sc.n, sc.c), device=dev)
+    gxyz = torch.empty((sc.n, 3), device=dev)
+    gpose = torch.zeros((1, 6), device=dev)
+    gintr = torch.zeros((1, 6), device=dev)
+    lib = A.load()
+    ps, pr, fs = pts.struct(), params.struct(), (A.adop_frame * 1)(fr.struct())
+    cs = A._cams_array([cam])
+    gp = (ct.c_void_p * 4)(*[g.data_ptr() for g in gimg])
+    wp, wn = A._ws_ptr(ws)
+
+    def step():
+        s = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        gpose.zero_()
+        gintr.zero_()
+        assert lib.adop_render_forward(ct.byref(ps), cs, 1, ct.byref(pr), fs, wp, wn, s) == 0
+        assert lib.adop_render_backward(ct.byref(ps), cs, 1, ct.byref(pr), fs, gp, gfeat.data_ptr(),
+                                        gxyz.data_ptr(), gpose.data_ptr(), gintr.data_ptr(), wp, wn, s) == 0
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(2):  # replays overwrite the same buffers with the same results
+        gfeat.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(fr.key.cpu().numpy().view(np.uint64), ref["keys"][0])
+        img = np.concatenate([im.cpu().numpy().ravel() for im in fr.images])
+        assert_close(img, ref["img"][0], RTOL_FEAT_F32, "image")
+        assert_close(gfeat.cpu().numpy(), ref["dfeat"], RTOL_GRAD, "dL/dtau")
+        assert_close(gxyz.cpu().numpy(), ref["dxyz"], RTOL_GRAD, "dL/dx")
+        assert_close(gpose.cpu().numpy()[0], ref["dpose"][0], RTOL_GRAD, "dL/dxi")
