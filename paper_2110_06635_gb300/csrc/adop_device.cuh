@@ -210,6 +210,13 @@ __device__ __forceinline__ bool camera(const DevCam& cam, float X0, float X1, fl
   const float r2 = __fadd_rn(__fmul_rn(xn, xn), __fmul_rn(yn, yn));
   const float d = __fadd_rn(
       1.0f, __fmul_rn(r2, __fadd_rn(cam.k1, __fmul_rn(r2, __fadd_rn(cam.k2, __fmul_rn(r2, cam.k3))))));
+  if (cam.p1 == 0.0f && cam.p2 == 0.0f) {
+    // no tangential terms: they are exact zeros for finite inputs, and a
+    // non-finite xn or yn fails the bounds test either way
+    u0 = __fadd_rn(__fmul_rn(cam.fx, __fmul_rn(xn, d)), cam.cx);
+    v0 = __fadd_rn(__fmul_rn(cam.fy, __fmul_rn(yn, d)), cam.cy);
+    return true;
+  }
   const float a = __fmul_rn(xn, yn);
   const float tx = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, cam.p1), a),
                              __fmul_rn(cam.p2, __fadd_rn(r2, __fmul_rn(2.0f, __fmul_rn(xn, xn)))));
