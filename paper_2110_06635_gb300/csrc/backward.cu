@@ -19,7 +19,9 @@
 //                  mask: warps compact their (point, layer) pairs in shared
 //                  memory and process them densely; with binning, the
 //                  visible points are visited 32x32-pixel screen tile by
-//                  tile, so the pixel records a warp reads stay in cache.
+//                  tile, so the pixel records a warp reads stay in cache,
+//                  and (gradients assigned) the points in no Lambda get
+//                  their zero gradients after the pairs.
 //   k_bin_*        count the visible points per screen tile, scan, scatter
 //                  their indices tile by tile.
 //   k_bwd_reduce   sums the block partials in a fixed order (deterministic).
