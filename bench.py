@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true", help="skip the 16-camera training step")
     ap.add_argument("--no-discard", action="store_true", help="skip the stochastic-discarding variant")
     ap.add_argument("--no-env", action="store_true", help="skip the environment-map variant")
+    ap.add_argument("--no-shuffle", action="store_true", help="skip the randomly ordered variant")
     ap.add_argument("--eager", action="store_true", help="time the step launched eagerly, not as a CUDA graph")
     ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -436,6 +437,33 @@ def run_ours(args, dist, rank, world):
             del wl
             torch.cuda.empty_cache()
     return results, clocks, device
+
+
+def bench_shuffled(device, steps: int, warmup: int, flush) -> dict:
+    """The headline workload with its points in a random order instead of
+    surface by surface (the paper sorts its clouds for locality): how much the
+    point order is worth.  The step is the same eager step as `kernel_ms`."""
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+    import scenes
+    sc, cams = scenes.config(2, shuffle=True)
+    wl = Workload(sc.n, "bf16", device, scene=sc, cam=cams[0])
+    sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(warmup):
+        wl.step(sp)
+    adop.adop_profile_enable(True)
+    adop.adop_profile_collect()
+    total_ms, _ = timed_steps(lambda: wl.step(sp), steps, flush, None, device)
+    ks = adop.adop_profile_collect()
+    adop.adop_profile_enable(False)
+    out = {"workload": "the headline view with the 5M points in a random order",
+           "value": round(wl.n * steps / (total_ms / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(total_ms / steps, 4),
+           "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_discard(device, steps: int, warmup: int, flush) -> dict:
@@ -834,6 +862,10 @@ def main():
         if not args.no_discard:
             fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
             line["stochastic_discard"] = bench_discard(device, args.steps, args.warmup, lambda: fb.zero_())
+            del fb
+        if not args.no_shuffle:
+            fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+            line["shuffled_points"] = bench_shuffled(device, args.steps, args.warmup, lambda: fb.zero_())
             del fb
         if not args.no_env:
             fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
