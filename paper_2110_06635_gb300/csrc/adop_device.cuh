@@ -355,6 +355,19 @@ __device__ __forceinline__ void atomic_add_vec(float* a, const float (&f)[C]) {
   }
 }
 
+// Programmatic dependent launch (sm_90+).  Every kernel that the library
+// launches with launch_pdl() calls this before its first memory access.  The
+// wait returns once the grids before it in the stream have completed and
+// their writes are visible, so the body runs exactly in stream order; the
+// trigger after it lets the next grid's blocks be placed on SMs as this grid's
+// last blocks retire (they wait in the same call), which hides the launch
+// latency between the kernels of a step.  Without a programmatic predecessor
+// both instructions do nothing.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Layer of a pixel index g in [0, off[levels]).
 __device__ __forceinline__ int layer_of(const DevCam& cam, int levels, int64_t g) {
   int l = 0;

@@ -34,6 +34,7 @@ namespace adop {
 template <int C>
 __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant__ LaunchCams cams,
                                                           const __grid_constant__ PointArgs a) {
+  pdl_entry();
   constexpr int GS = g_stride(C);
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
@@ -256,6 +257,7 @@ template <int C, typename TF>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constant__ LaunchCams cams,
                                                             const __grid_constant__ PointArgs a,
                                                             const __grid_constant__ BwdArgs b) {
+  pdl_entry();
   constexpr int GS = g_stride(C);
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
@@ -345,6 +347,7 @@ template <int C, typename TF, bool BINNED>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant__ LaunchCams cams,
                                                            const __grid_constant__ PointArgs a,
                                                            const __grid_constant__ BwdArgs b) {
+  pdl_entry();
   constexpr int GS = g_stride(C);
   constexpr int PS = (6 + C) | 1;  // per point: z, u0, v0, X (camera space), tau (odd stride: no bank conflicts)
   constexpr int AS = (C + 2) | 1;  // per point: sum of G/|Lambda|, du0, dv0
@@ -522,6 +525,7 @@ __device__ __forceinline__ void lane_run(uint32_t key, bool active, int lane, in
 
 __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ LaunchCams cams,
                                                         const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -539,6 +543,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ 
 // One block per camera: exclusive scan of the tile counts; the counts become
 // the scatter cursors (= the offsets).
 __global__ void __launch_bounds__(1024) k_bin_scan(const __grid_constant__ LaunchCams cams) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.x];
   __shared__ int32_t warp_sum[32];
   const int T = cam.tiles;
@@ -580,6 +585,7 @@ template <int C>
 __global__ void __launch_bounds__(kThreads) k_bin_scatter(const __grid_constant__ LaunchCams cams,
                                                           const __grid_constant__ PointArgs a,
                                                           const __grid_constant__ BwdArgs b) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -613,6 +619,7 @@ __device__ __forceinline__ void chunk_of(int64_t n, int64_t& c0, int64_t& c1) {
 
 __global__ void __launch_bounds__(kThreads) k_bin_count_blk(const __grid_constant__ LaunchCams cams,
                                                             const __grid_constant__ PointArgs a) {
+  pdl_entry();
   extern __shared__ int32_t bins[];
   const DevCam& cam = cams.c[blockIdx.y];
   const int T = cam.tiles;
@@ -634,6 +641,7 @@ template <int C>
 __global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_constant__ LaunchCams cams,
                                                               const __grid_constant__ PointArgs a,
                                                               const __grid_constant__ BwdArgs b) {
+  pdl_entry();
   extern __shared__ int32_t bins[];  // counts, then this block's next slot per tile
   const DevCam& cam = cams.c[blockIdx.y];
   const int T = cam.tiles;
@@ -659,6 +667,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_const
 // One block per camera, warp k sums element k over all block partials.
 __global__ void __launch_bounds__(384) k_bwd_reduce(const float* __restrict__ partials, int blocks_x,
                                                     float* grad_pose, float* grad_intr) {
+  pdl_entry();
   const int cam = blockIdx.x;
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
   float v = 0.0f;
@@ -675,8 +684,9 @@ __global__ void __launch_bounds__(384) k_bwd_reduce(const float* __restrict__ pa
 }
 
 cudaError_t launch_bwd_prepass(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
-  ADOP_DISPATCH_C(c, k_bwd_prepass<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, e = launch_pdl(k_bwd_prepass<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a));
+  return e;
 }
 
 cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c,
@@ -688,14 +698,18 @@ cudaError_t launch_bwd_points(const LaunchCams& cams, const PointArgs& a, const 
     dense = dense && cams.c[k].vis != nullptr;
     binned = binned && cams.c[k].bin_list != nullptr;
   }
+  cudaError_t e = cudaSuccess;
   if (dense && binned) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF, true><<<grid, kThreads, 0, s>>>(cams, a, b)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_bwd_items<kC, TF, true>, grid, kThreads, 0, s, cams, a,
+                                                              b)));
   } else if (dense) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_items<kC, TF, false><<<grid, kThreads, 0, s>>>(cams, a, b)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_bwd_items<kC, TF, false>, grid, kThreads, 0, s, cams, a,
+                                                              b)));
   } else {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_bwd_points<kC, TF><<<grid, kThreads, 0, s>>>(cams, a, b)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_bwd_points<kC, TF>, grid, kThreads, 0, s, cams, a,
+                                                              b)));
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs& b, int c, cudaStream_t s) {
@@ -711,22 +725,21 @@ cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs
     int64_t want = (int64_t)num_sms() * kBinBlocksPerSm;
     want = (want + a.ncam - 1) / a.ncam;
     const dim3 grid((unsigned)(want < 1 ? 1 : want), a.ncam);
-    k_bin_count_blk<<<grid, kThreads, smem, s>>>(cams, a);
-    k_bin_scan<<<a.ncam, 1024, 0, s>>>(cams);
-    ADOP_DISPATCH_C(c, k_bin_scatter_blk<kC><<<grid, kThreads, smem, s>>>(cams, a, b));
-  } else {
-    const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
-    k_bin_count<<<grid, kThreads, 0, s>>>(cams, a);
-    k_bin_scan<<<a.ncam, 1024, 0, s>>>(cams);
-    ADOP_DISPATCH_C(c, k_bin_scatter<kC><<<grid, kThreads, 0, s>>>(cams, a, b));
+    cudaError_t e = launch_pdl(k_bin_count_blk, grid, kThreads, smem, s, cams, a);
+    if (e == cudaSuccess) e = launch_pdl(k_bin_scan, dim3(a.ncam), dim3(1024), 0, s, cams);
+    if (e == cudaSuccess) ADOP_DISPATCH_C(c, e = launch_pdl(k_bin_scatter_blk<kC>, grid, kThreads, smem, s, cams, a, b));
+    return e;
   }
-  return cudaGetLastError();
+  const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
+  cudaError_t e = launch_pdl(k_bin_count, grid, kThreads, 0, s, cams, a);
+  if (e == cudaSuccess) e = launch_pdl(k_bin_scan, dim3(a.ncam), dim3(1024), 0, s, cams);
+  if (e == cudaSuccess) ADOP_DISPATCH_C(c, e = launch_pdl(k_bin_scatter<kC>, grid, kThreads, 0, s, cams, a, b));
+  return e;
 }
 
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s) {
-  k_bwd_reduce<<<ncam, 384, 0, s>>>(partials, blocks_x, grad_pose, grad_intr);
-  return cudaGetLastError();
+  return launch_pdl(k_bwd_reduce, dim3(ncam), dim3(384), 0, s, partials, blocks_x, grad_pose, grad_intr);
 }
 
 }  // namespace adop

@@ -20,6 +20,7 @@ namespace {
 template <int C, typename TO>
 __global__ void __launch_bounds__(kThreads) k_env_fill(const __grid_constant__ LaunchCams cams,
                                                        const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kThreads) k_env_fill(const __grid_constant__ L
 template <int C>
 __global__ void __launch_bounds__(kThreads) k_env_grad(const __grid_constant__ LaunchCams cams,
                                                        const __grid_constant__ PointArgs a, float* grad_env) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -99,13 +101,16 @@ adop_status fail(adop_status st, const char* msg) {
 }  // namespace
 
 cudaError_t launch_env_fill(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, k_env_fill<kC, TO><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_pdl(k_env_fill<kC, TO>, pixel_grid(cams, a), kThreads, 0, s,
+                                                            cams, a)));
+  return e;
 }
 
 cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s) {
-  ADOP_DISPATCH_C(c, k_env_grad<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a, grad_env));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, e = launch_pdl(k_env_grad<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a, grad_env));
+  return e;
 }
 
 }  // namespace adop

@@ -34,6 +34,7 @@ int point_blocks(int64_t n, int ncam) {
 template <int C>
 __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     float X0, X1, X2, u0, v0, zd;
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
 template <int C, typename TF, int kL>
 __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ LaunchCams cams,
                                                     const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const __grid_constant__ Laun
 template <int C, typename TO>
 __global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ LaunchCams cams,
                                                         const __grid_constant__ PointArgs a) {
+  pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -191,30 +195,34 @@ dim3 pixel_grid(const LaunchCams& cams, const PointArgs& a) {
 }
 
 cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
-  ADOP_DISPATCH_C(c, k_clear<kC><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, e = launch_pdl(k_clear<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a));
+  return e;
 }
 
 cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  k_depth<<<dim3(point_blocks(a.n, a.ncam), a.ncam), kThreads, 0, s>>>(cams, a);
-  return cudaGetLastError();
+  return launch_pdl(k_depth, dim3(point_blocks(a.n, a.ncam), a.ncam), kThreads, 0, s, cams, a);
 }
 
 cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
+  cudaError_t e = cudaSuccess;
   if (a.levels <= 4) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF, 4><<<grid, kThreads, 0, s>>>(cams, a)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_accum<kC, TF, 4>, grid, kThreads, 0, s, cams, a)));
   } else {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, k_accum<kC, TF, ADOP_MAX_LEVELS><<<grid, kThreads, 0, s>>>(cams, a)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_accum<kC, TF, ADOP_MAX_LEVELS>, grid, kThreads, 0, s,
+                                                              cams, a)));
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_normalize(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, k_normalize<kC, TO><<<pixel_grid(cams, a), kThreads, 0, s>>>(cams, a)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_pdl(k_normalize<kC, TO>, pixel_grid(cams, a), kThreads, 0, s,
+                                                            cams, a)));
+  return e;
 }
 
 }  // namespace adop

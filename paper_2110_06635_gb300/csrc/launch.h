@@ -4,9 +4,31 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "adop_device.cuh"
 
 namespace adop {
+
+// Launches kernel k on stream s as a programmatic dependent of the work before
+// it in the stream.  The kernel must call pdl_entry() before its first memory
+// access (a CPU test checks every kernel launched this way); it then runs in
+// stream order, while its launch overlaps the end of the previous kernel.  In
+// a captured CUDA graph the dependency becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // Arguments shared by the point kernels of one launch.
 struct PointArgs {

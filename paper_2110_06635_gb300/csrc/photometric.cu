@@ -31,6 +31,7 @@ template <int C>
 __global__ void __launch_bounds__(kThreads) k_photo_grad(const __grid_constant__ LaunchCams cams,
                                                          const __grid_constant__ PointArgs a,
                                                          const __grid_constant__ PhotoArgs pa) {
+  pdl_entry();
   extern __shared__ float hist[];  // 3 x crf_n
   __shared__ float sm[kThreads / 32][kPhotoParams];
   const DevCam& cam = cams.c[blockIdx.y];
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_photo_grad(const __grid_constant__
 
 // One block per camera; warp k sums parameter k over the block partials.
 __global__ void k_photo_reduce(const float* __restrict__ partials, int blocks, float* grad_photo) {
+  pdl_entry();
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
   float s = 0.0f;
   for (int b = lane; b < blocks; b += 32) s += partials[((int64_t)blockIdx.x * blocks + b) * kPhotoParams + k];
@@ -121,8 +123,9 @@ adop_status fail(adop_status st, const char* msg) {
 
 cudaError_t launch_photo(const LaunchCams& lc, const PointArgs& a, const PhotoArgs& pa, int c, size_t smem,
                          cudaStream_t s) {
-  ADOP_DISPATCH_C(c, k_photo_grad<kC><<<dim3(kPhotoBlocks, a.ncam), kThreads, smem, s>>>(lc, a, pa));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  ADOP_DISPATCH_C(c, e = launch_pdl(k_photo_grad<kC>, dim3(kPhotoBlocks, a.ncam), kThreads, smem, s, lc, a, pa));
+  return e;
 }
 
 }  // namespace
@@ -187,8 +190,9 @@ adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, co
     const size_t smem = sizeof(float) * 3 * (size_t)max_lut;
     if ((e = timed("photo_grad", s, [&] { return launch_photo(lc, a, pa, c, smem, s); })) != cudaSuccess)
       return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
-    k_photo_reduce<<<nc, 32 * kPhotoParams, 0, s>>>(partials, kPhotoBlocks, grad_photo + (size_t)k0 * kPhotoParams);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = launch_pdl(k_photo_reduce, dim3(nc), dim3(32 * kPhotoParams), 0, s, partials, (int)kPhotoBlocks,
+                        grad_photo + (size_t)k0 * kPhotoParams)) != cudaSuccess)
+      return fail(ADOP_ERR_CUDA, cudaGetErrorString(e));
   }
   return ADOP_OK;
 }
