@@ -685,7 +685,8 @@ __global__ void __launch_bounds__(384) k_bwd_reduce(const float* __restrict__ pa
 
 cudaError_t launch_bwd_prepass(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  ADOP_DISPATCH_C(c, e = launch_pdl(k_bwd_prepass<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a));
+  const int64_t px = most_pixels(cams, a);
+  ADOP_DISPATCH_C(c, e = launch_strided(k_bwd_prepass<kC>, px, a.ncam, kPixelWaves, 0, s, cams, a));
   return e;
 }
 

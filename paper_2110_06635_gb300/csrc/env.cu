@@ -102,14 +102,16 @@ adop_status fail(adop_status st, const char* msg) {
 
 cudaError_t launch_env_fill(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_pdl(k_env_fill<kC, TO>, pixel_grid(cams, a), kThreads, 0, s,
-                                                            cams, a)));
+  const int64_t px = most_pixels(cams, a);
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_strided(k_env_fill<kC, TO>, px, a.ncam, kPixelWaves, 0, s,
+                                                                cams, a)));
   return e;
 }
 
 cudaError_t launch_env_grad(const LaunchCams& cams, const PointArgs& a, int c, float* grad_env, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  ADOP_DISPATCH_C(c, e = launch_pdl(k_env_grad<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a, grad_env));
+  const int64_t px = most_pixels(cams, a);
+  ADOP_DISPATCH_C(c, e = launch_strided(k_env_grad<kC>, px, a.ncam, kPixelWaves, 0, s, cams, a, grad_env));
   return e;
 }
 

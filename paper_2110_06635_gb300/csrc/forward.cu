@@ -4,7 +4,8 @@
 // implementation details), preceded by a clear of the per-pixel state.
 //
 // Work decomposition: blockIdx.y selects the camera; blocks stride over
-// points (or pixels) with a grid sized to a few waves of the GPU's SMs.
+// points (or pixels) with a grid of whole waves of the kernel's resident
+// blocks over the GPU's SMs (stride_grid).
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -26,6 +27,34 @@ int point_blocks(int64_t n, int ncam) {
   const int64_t cap = ((int64_t)num_sms() * 8 + ncam - 1) / ncam;
   int64_t b = want < cap ? want : cap;
   return (int)(b < 1 ? 1 : b);
+}
+
+namespace {
+// Resident blocks per SM of kernel k (occupancy calculator), cached per
+// calling thread: a launch asks the runtime once per kernel and thread.
+int resident_blocks(const void* k, size_t smem) {
+  struct Entry {
+    const void* k;
+    size_t smem;
+    int n;
+  };
+  constexpr int kEntries = 256;
+  static thread_local Entry cache[kEntries];
+  static thread_local int used = 0;
+  for (int i = 0; i < used; ++i)
+    if (cache[i].k == k && cache[i].smem == smem) return cache[i].n;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess || n < 1) n = 1;
+  if (used < kEntries) cache[used++] = Entry{k, smem, n};
+  return n;
+}
+}  // namespace
+
+dim3 stride_grid(const void* k, int64_t work, int ncam, int waves, size_t smem) {
+  const int64_t want = (work + kThreads - 1) / kThreads;
+  const int64_t cap = ((int64_t)num_sms() * resident_blocks(k, smem) * waves + ncam - 1) / ncam;
+  const int64_t b = want < cap ? want : cap;
+  return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)ncam);
 }
 
 // ---------------------------------------------------------------------------
@@ -185,43 +214,42 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ 
   }
 }
 
-dim3 pixel_grid(const LaunchCams& cams, const PointArgs& a) {
+int64_t most_pixels(const LaunchCams& cams, const PointArgs& a) {
   int64_t most = 0;
   for (int k = 0; k < a.ncam; ++k) most = cams.c[k].off[a.levels] > most ? cams.c[k].off[a.levels] : most;
-  int64_t want = (most + kThreads - 1) / kThreads;
-  int64_t cap = ((int64_t)num_sms() * 8 + a.ncam - 1) / a.ncam;
-  int64_t b = want < cap ? want : cap;
-  return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)a.ncam);
+  return most;
 }
 
 cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  ADOP_DISPATCH_C(c, e = launch_pdl(k_clear<kC>, pixel_grid(cams, a), kThreads, 0, s, cams, a));
+  const int64_t px = most_pixels(cams, a);
+  ADOP_DISPATCH_C(c, e = launch_strided(k_clear<kC>, px, a.ncam, kPixelWaves, 0, s, cams, a));
   return e;
 }
 
 cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  return launch_pdl(k_depth, dim3(point_blocks(a.n, a.ncam), a.ncam), kThreads, 0, s, cams, a);
+  return launch_strided(k_depth, a.n, a.ncam, kPointWaves, 0, s, cams, a);
 }
 
 cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  const dim3 grid(point_blocks(a.n, a.ncam), a.ncam);
   cudaError_t e = cudaSuccess;
   if (a.levels <= 4) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_accum<kC, TF, 4>, grid, kThreads, 0, s, cams, a)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, 4>, a.n, a.ncam, kPointWaves, 0,
+                                                                  s, cams, a)));
   } else {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_pdl(k_accum<kC, TF, ADOP_MAX_LEVELS>, grid, kThreads, 0, s,
-                                                              cams, a)));
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, ADOP_MAX_LEVELS>, a.n, a.ncam,
+                                                                  kPointWaves, 0, s, cams, a)));
   }
   return e;
 }
 
 cudaError_t launch_normalize(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype od, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_pdl(k_normalize<kC, TO>, pixel_grid(cams, a), kThreads, 0, s,
-                                                            cams, a)));
+  const int64_t px = most_pixels(cams, a);
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(od, TO, e = launch_strided(k_normalize<kC, TO>, px, a.ncam, kPixelWaves, 0, s,
+                                                                cams, a)));
   return e;
 }
 

@@ -62,8 +62,35 @@ struct BwdArgs {
 };
 
 int num_sms();
+// Blocks for a point kernel's items pass: 8 per SM (two waves of its 4
+// resident blocks), shared by the ncam cameras of grid.y.
 int point_blocks(int64_t n, int ncam);
-dim3 pixel_grid(const LaunchCams& cams, const PointArgs& a);
+// Most pyramid pixels of any camera in the launch.
+int64_t most_pixels(const LaunchCams& cams, const PointArgs& a);
+// Grid of a grid-stride kernel k (kThreads threads, smem bytes of dynamic
+// shared memory) over `work` items per camera: enough blocks for the work, at
+// most `waves` whole waves of the kernel's resident blocks over all SMs,
+// shared by the ncam cameras of grid.y.  Whole waves: a grid of 8 blocks per
+// SM for a kernel that holds 5 ran its last 0.6 wave on 60% of the block
+// slots.  Many waves rather than one: the work per item varies widely (a
+// point outside the view costs a projection, a visible one up to four key
+// reads and atomics), and with one long-lived block per slot the SMs whose
+// blocks drew cheap items idle while the slowest block finishes; with many
+// short blocks the block scheduler refills them.  (5M-point 1080p step: depth
+// 72 -> 64 us and accumulate 100 -> 91 us at unchanged DRAM traffic and L2
+// hit rate; more waves than these were slower again.)
+constexpr int kPointWaves = 10;  // k_depth, k_accum
+constexpr int kPixelWaves = 6;   // k_clear, k_normalize, k_bwd_prepass, k_env_*
+dim3 stride_grid(const void* k, int64_t work, int ncam, int waves, size_t smem);
+
+// launch_pdl of a grid-stride kernel over `work` items per camera, on the
+// stride_grid() of that kernel.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_strided(void (*k)(KArgs...), int64_t work, int ncam, int waves, size_t smem, cudaStream_t s,
+                           Args&&... args) {
+  return launch_pdl(k, stride_grid((const void*)k, work, ncam, waves, smem), dim3(kThreads), smem, s,
+                    std::forward<Args>(args)...);
+}
 
 cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s);
 cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s);

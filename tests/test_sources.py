@@ -1,10 +1,11 @@
 """Checks on the CUDA sources that need no GPU.
 
-Every kernel launched with launch_pdl() (programmatic dependent launch) must
-call pdl_entry() before its first memory access: without the grid-dependency
-wait at its start the kernel could read what the kernel before it is still
-writing.  The check is textual: for each kernel name passed to launch_pdl, its
-__global__ definition's body must open with `pdl_entry();`."""
+Every kernel launched with launch_pdl() or launch_strided() (programmatic
+dependent launch) must call pdl_entry() before its first memory access:
+without the grid-dependency wait at its start the kernel could read what the
+kernel before it is still writing.  The check is textual: for each kernel name
+passed to either, its __global__ definition's body must open with
+`pdl_entry();`."""
 import os
 import re
 
@@ -25,7 +26,7 @@ def _pdl_launched(srcs):
     for fn, s in srcs.items():
         if fn == "launch.h":
             continue
-        for m in re.finditer(r"launch_pdl\(\s*(k_\w+)", s):
+        for m in re.finditer(r"launch_(?:pdl|strided)\(\s*(k_\w+)", s):
             names.add(m.group(1))
     return names
 
