@@ -210,7 +210,7 @@ __device__ __forceinline__ void block_partials(const BwdArgs& b, float (&red)[12
     float v = 0.0f;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) v += sm[w][threadIdx.x];
-    b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + threadIdx.x] = v;
+    b.partials[((int64_t)blockIdx.y * 12 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
   }
 }
 
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
       for (int j = lane; j < kThreads; j += 32) t += s_red[k][j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) b.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 12 + k] = t;
+      if (lane == 0) b.partials[((int64_t)blockIdx.y * 12 + k) * gridDim.x + blockIdx.x] = t;
     }
   }
 }
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(const __grid_constant_
 // one per run of lanes (which serialises on the few tiles that a surface
 // being streamed covers).
 constexpr int kBinSmemTiles = 8192;
-constexpr int kBinBlocksPerSm = 4;
+constexpr int kBinBlocksPerSm = 8;
 
 __device__ __forceinline__ void chunk_of(int64_t n, int64_t& c0, int64_t& c1) {
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -664,21 +664,33 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_const
   }
 }
 
-// One block per camera, warp k sums element k over all block partials.
-__global__ void __launch_bounds__(384) k_bwd_reduce(const float* __restrict__ partials, int blocks_x,
-                                                    float* grad_pose, float* grad_intr) {
+// Block (k, camera) sums element k of the pose / intrinsics terms over all
+// block partials (laid out element-major, [camera][12][block], so that the
+// loads coalesce): each thread a strided share, then the warps, then the
+// warp sums in order -- a fixed order, so the result is deterministic.
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads) k_bwd_reduce(const float* __restrict__ partials, int blocks_x,
+                                                               float* grad_pose, float* grad_intr) {
   pdl_entry();
-  const int cam = blockIdx.x;
-  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+  __shared__ float sm[kReduceThreads / 32];
+  const int k = blockIdx.x, cam = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* pk = partials + ((int64_t)cam * 12 + k) * blocks_x;
   float v = 0.0f;
-  for (int bi = lane; bi < blocks_x; bi += 32) v += partials[((int64_t)cam * blocks_x + bi) * 12 + k];
+  for (int bi = threadIdx.x; bi < blocks_x; bi += kReduceThreads) v += pk[bi];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) {
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kReduceThreads / 32; ++w) t += sm[w];
     if (k < 6) {
-      if (grad_pose) grad_pose[cam * 6 + k] += v;
+      if (grad_pose) grad_pose[cam * 6 + k] += t;
     } else if (grad_intr) {
-      grad_intr[cam * 6 + k - 6] += v;
+      grad_intr[cam * 6 + k - 6] += t;
     }
   }
 }
@@ -740,7 +752,8 @@ cudaError_t launch_bin(const LaunchCams& cams, const PointArgs& a, const BwdArgs
 
 cudaError_t launch_bwd_reduce(const float* partials, int ncam, int blocks_x, float* grad_pose,
                               float* grad_intr, cudaStream_t s) {
-  return launch_pdl(k_bwd_reduce, dim3(ncam), dim3(384), 0, s, partials, blocks_x, grad_pose, grad_intr);
+  return launch_pdl(k_bwd_reduce, dim3(12, ncam), dim3(kReduceThreads), 0, s, partials, blocks_x, grad_pose,
+                    grad_intr);
 }
 
 }  // namespace adop

@@ -56,7 +56,7 @@ enum GradMode : int32_t { kGradAssign = 0, kGradAccumulate = 1, kGradAtomic = 2 
 struct BwdArgs {
   float* grad_feat;
   float* grad_xyz;
-  float* partials;      // [ncam][blocks_x][12] pose (6) + intrinsics (6) block sums
+  float* partials;      // [ncam][12][blocks_x] pose (6) + intrinsics (6) block sums
   int32_t mode;         // GradMode
   int32_t all_projected;
 };
