@@ -139,8 +139,8 @@ constexpr int accum_min_blocks() {
 }
 
 template <int C, typename TF, int kL>
-__global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>()) k_accum(const __grid_constant__ LaunchCams cams,
-                                                    const __grid_constant__ PointArgs a) {
+__global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>())
+    k_accum(const __grid_constant__ LaunchCams cams, const __grid_constant__ PointArgs a) {
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const TF* feat = reinterpret_cast<const TF*>(a.feat);
