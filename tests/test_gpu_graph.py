@@ -62,3 +62,64 @@ def test_captured_step_equals_eager_step(adop):
         assert_close(gfeat.cpu().numpy(), ref["dfeat"], RTOL_GRAD, "dL/dtau")
         assert_close(gxyz.cpu().numpy(), ref["dxyz"], RTOL_GRAD, "dL/dx")
         assert_close(gpose.cpu().numpy()[0], ref["dpose"][0], RTOL_GRAD, "dL/dxi")
+
+
+_FIRST_CAPTURE = r"""
+import ctypes as ct, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[2])
+import scenes
+import paper_2110_06635_gb300 as adop
+from paper_2110_06635_gb300 import _abi as A
+adop.build(); adop.load()
+sc, cams = scenes.config(1)
+cam = cams[0]
+dev = "cuda"
+pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+params = adop.Params(4, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+fr = adop.Frame.alloc(cam, sc.c, 4, torch.float32, True, dev, sc.n)
+ws = adop.alloc_workspace(pts, [cam], params, None, dev)
+G = scenes.upstream_grad(cam.w, cam.h, 4, sc.c, 43)
+gimg = [torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in G]
+gfeat = torch.empty((sc.n, sc.c), device=dev)
+gxyz = torch.empty((sc.n, 3), device=dev)
+lib = A.load()
+ps, pr, fs = pts.struct(), params.struct(), (A.adop_frame * 1)(fr.struct())
+cs = A._cams_array([cam])
+gp = (ct.c_void_p * 4)(*[g.data_ptr() for g in gimg])
+wp, wn = A._ws_ptr(ws)
+def step():
+    s = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.adop_render_forward(ct.byref(ps), cs, 1, ct.byref(pr), fs, wp, wn, s) == 0
+    assert lib.adop_render_backward(ct.byref(ps), cs, 1, ct.byref(pr), fs, gp, gfeat.data_ptr(), gxyz.data_ptr(),
+                                    None, None, wp, wn, s) == 0
+torch.cuda.synchronize()
+graph = torch.cuda.CUDAGraph()
+with torch.cuda.graph(graph):  # the library's first launches happen inside the capture
+    step()
+graph.replay()
+torch.cuda.synchronize()
+k1, f1 = fr.key.clone(), gfeat.clone()
+step()
+torch.cuda.synchronize()
+assert torch.equal(k1, fr.key)
+# dL/dtau sums each point's layers in an order that follows the binning's
+# atomic order, so the two runs may differ in the last bits
+d = (f1 - gfeat).abs().max().item()
+ref = max(gfeat.abs().max().item(), 1e-30)
+assert d <= 1e-5 * ref, (d, ref)
+print("ok")
+"""
+
+
+def test_capture_before_any_eager_launch(adop):
+    """A process whose first library launches are inside a graph capture (the
+    grid sizes then come from occupancy queries made during the capture)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CAPTURE, root, os.path.join(root, "tests")],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-4000:]
