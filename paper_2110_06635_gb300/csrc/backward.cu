@@ -24,7 +24,9 @@
 //                  their zero gradients after the pairs.
 //   k_bin_*        count the visible points per screen tile, scan, scatter
 //                  their indices tile by tile.
-//   k_bwd_reduce   sums the block partials in a fixed order (deterministic).
+//   k_bwd_reduce   sums the block partials in a fixed order (no float atomics
+//                  across blocks; the partials themselves follow the order in
+//                  which the binning lists the points).
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter_blk(const __grid_const
 // Block (k, camera) sums element k of the pose / intrinsics terms over all
 // block partials (laid out element-major, [camera][12][block], so that the
 // loads coalesce): each thread a strided share, then the warps, then the
-// warp sums in order -- a fixed order, so the result is deterministic.
+// warp sums in order: a fixed order for given partials.
 constexpr int kReduceThreads = 256;
 
 __global__ void __launch_bounds__(kReduceThreads) k_bwd_reduce(const float* __restrict__ partials, int blocks_x,
