@@ -37,7 +37,7 @@ struct DevCam {
   void* image[ADOP_MAX_LEVELS];
   const float* grad[ADOP_MAX_LEVELS];
   float* acc;    // pixel-major FP32 sums, c floats per pixel
-  float* info;   // backward: per pixel {z_min, |Lambda|, <G, I>, 0}
+  float* info;   // backward: per pixel {z_min, 1/(1+|Lambda|) (1: empty), <G, I>, 1/|Lambda|}
   float* gpm;    // backward: upstream gradient, pixel-major, g_stride(c) floats per pixel
   uint32_t* vis;  // per point: layer mask (bits 0-7) | layer-0 screen tile << 8 (or NULL)
   // screen-tile binning of the visible points for the backward pass

@@ -56,8 +56,10 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     if (n == 0 && !a.env) {
 #pragma unroll
       for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
-    } else if (n != 0) {  // (an empty pixel's acc holds the environment map's value, kept by k_env_fill)
-      const float rn = __frcp_rn((float)n);  // one reciprocal per pixel (within 2 ulp of the quotient)
+    }
+    // one reciprocal per pixel (within 2 ulp of the quotient); 0 for an empty pixel
+    const float rn = n != 0 ? __frcp_rn((float)n) : 0.0f;
+    if (n != 0) {  // (an empty pixel's acc holds the environment map's value, kept by k_env_fill)
 #pragma unroll
       for (int k = 0; k < C; ++k) I[k] *= rn;
     }
@@ -75,8 +77,11 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     float gi = 0.0f;
 #pragma unroll
     for (int k = 0; k < C; ++k) gi = fmaf(G[k], I[k], gi);
+    // the reciprocals that the point pass needs, computed once here: 1/(1+|Lambda|)
+    // for a neighbour's joins-the-blend case (exactly 1 for an empty pixel, at
+    // most 1/2 otherwise) and 1/|Lambda| for the feature gradient
     reinterpret_cast<float4*>(cam.info)[g] =
-        make_float4(__uint_as_float((uint32_t)(key >> 32)), (float)n, gi, 0.0f);
+        make_float4(__uint_as_float((uint32_t)(key >> 32)), __frcp_rn(1.0f + (float)n), gi, rn);
     store_row<GS>(cam.gpm + g * GS, G);  // (rows of GS floats in a 256-byte-aligned workspace block)
   }
 }
@@ -239,10 +244,10 @@ __device__ __forceinline__ void spatial_grad(const DevCam& cam, const float4* __
     cq[s] = 0.0f;
     if (gq[s] < 0) continue;
     float wgt;
-    if (iq[s].y == 0.0f) wgt = 1.0f;                            // empty: overwrite background
+    if (iq[s].y == 1.0f) wgt = 1.0f;                            // empty: 1/(1+0) = 1, overwrite
     else if (z > __fmul_rn(iq[s].x, a1)) wgt = 0.0f;            // behind the target surface
     else if (__fmul_rn(z, a1) < iq[s].x) wgt = 1.0f;            // in front: replaces the mean
-    else wgt = __frcp_rn(1.0f + iq[s].y);                        // joins the fuzzy blend
+    else wgt = iq[s].y;                                          // joins the fuzzy blend: 1/(1+|Lambda|)
     if (wgt == 0.0f) continue;
     float G[GS];
     load_keep_row<GS>(cam.gpm + gq[s] * GS, G, pol);
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_points(const __grid_constan
             float G[GS];
             load_vec<GS>(cam.gpm + gp * GS, G);
 #pragma unroll
-            for (int k = 0; k < C; ++k) gf[k] += G[k] * __frcp_rn(ip.y);
+            for (int k = 0; k < C; ++k) gf[k] += G[k] * ip.w;  // ip.w = f32(1/|Lambda|)
             touched = true;
           }
           if (!(vis || b.all_projected) || !spatial_out) continue;
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_items(const __grid_constant
           float G[GS];
           load_keep_row<GS>(cam.gpm + gp * GS, G, pol);
 #pragma unroll
-          for (int c = 0; c < C; ++c) v[c] = G[c] * __frcp_rn(ip.y);
+          for (int c = 0; c < C; ++c) v[c] = G[c] * ip.w;  // ip.w = f32(1/|Lambda|)
           if (spatial_out) {
             float tau[C];
 #pragma unroll
