@@ -125,16 +125,59 @@ def timed_steps(step, k: int, flush=None, dist=None, device="cuda"):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
+class Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes; no
+    package needed): one GPU's SM clock, its maximum and the clock-event
+    reason mask.  Nothing is set.  Raises OSError where NVML is missing."""
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
+    CLOCK_SM = 1
+
+    def __init__(self, uuid: str):
+        import ctypes as ct
+        self.ct = ct
+        self.lib = ct.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ct.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ct.byref(self.dev)) != 0:
+            self.lib.nvmlShutdown()
+            raise OSError(f"no NVML device {uuid}")
+        self.reasons_fn = (getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or
+                           self.lib.nvmlDeviceGetCurrentClocksThrottleReasons)
+
+    def sample(self):
+        """(SM MHz, max SM MHz, reason mask), or None if a query failed."""
+        ct = self.ct
+        c, m, r = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if (self.lib.nvmlDeviceGetClockInfo(self.dev, self.CLOCK_SM, ct.byref(c)) != 0 or
+                self.lib.nvmlDeviceGetMaxClockInfo(self.dev, self.CLOCK_SM, ct.byref(m)) != 0 or
+                self.reasons_fn(self.dev, ct.byref(r)) != 0):
+            return None
+        return c.value, m.value, r.value
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
+    """Clocks and throttle reasons during a timed region: `nvidia-smi -lms 200`
+    (started, and its first line awaited, before the region) plus NVML polled
+    every 1 ms from a thread, so that a region of a few milliseconds still
+    gets samples.  Only the samples taken inside the `with` body count."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_id: str):
+    def __init__(self, gpu_id: str, poll_s: float = 0.001):
         self.gpu_id = gpu_id
+        self.poll_s = poll_s
         self.proc = None
         self.lines = []
+        self.nvml_samples = []
+        self.nvml = None
         self.error = ""
+        self.stop = threading.Event()
 
     def __enter__(self):
         try:
@@ -146,13 +189,37 @@ class ClockSampler:
         except (OSError, ValueError) as e:
             self.proc = None
             self.error = repr(e)
+        try:
+            self.nvml = Nvml(self.gpu_id)
+            self.poller = threading.Thread(target=self._poll, daemon=True)
+            self.poller.start()
+        except (OSError, AttributeError) as e:
+            self.nvml = None
+            self.error = (self.error + " " + repr(e)).strip()
+        t0 = time.time()
+        while self.proc is not None and not self.lines and self.proc.poll() is None and time.time() - t0 < 3.0:
+            time.sleep(0.01)
+        self.lines.clear()  # (the region starts here)
+        self.nvml_samples.clear()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def _poll(self):
+        while not self.stop.is_set():
+            v = self.nvml.sample()
+            if v is not None:
+                self.nvml_samples.append(v)
+            time.sleep(self.poll_s)
+
     def __exit__(self, *exc):
+        n_lines = len(self.lines)
+        self.stop.set()
+        if self.nvml is not None:
+            self.poller.join(timeout=2)
+            self.nvml.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -160,10 +227,10 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.thread.join(timeout=2)
+        del self.lines[n_lines:]  # lines printed after the region do not count
 
     def summary(self):
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
@@ -173,14 +240,22 @@ class ClockSampler:
                 smax.append(float(f[1]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
+            for nm, v in zip(self.REASONS, f[4:8]):
                 if v.lower() == "active":
+                    reasons.add(nm)
+        n_smi = len(sm)
+        bits = dict(zip(self.REASONS, (Nvml.HW_SLOWDOWN, Nvml.HW_THERMAL, Nvml.SW_THERMAL, Nvml.SW_POWER_CAP)))
+        for c, m, r in self.nvml_samples:
+            sm.append(float(c))
+            smax.append(float(m))
+            for nm, b in bits.items():
+                if r & b:
                     reasons.add(nm)
         if not sm:
             why = self.error or (self.lines[0][:160] if self.lines else "no output")
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "error": why}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_nvidia_smi": n_smi, "samples_nvml": len(self.nvml_samples)}
 
 
 def gpu_index(device) -> str:

@@ -60,3 +60,32 @@ def test_algorithmic_bytes_model():
     assert bench.algorithmic_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
     with pytest.raises(KeyError):
         bench.algorithmic_bytes("nope", n, px, c, 2, 2)
+
+
+def test_clock_summary_merges_nvidia_smi_and_nvml():
+    """The clock record of a timed region: nvidia-smi lines and NVML samples
+    (reason bits decoded) merge into one median, maximum and reason set."""
+    import bench
+    cs = bench.ClockSampler("GPU-test")
+    cs.lines = ["2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Active"]
+    cs.nvml_samples = [(2070, 2070, 0), (2055, 2070, bench.Nvml.SW_POWER_CAP), (2070, 2070, 0)]
+    s = cs.summary()
+    assert s["samples"] == 4 and s["samples_nvidia_smi"] == 1 and s["samples_nvml"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.nvml_samples = [(1500, 2070, bench.Nvml.HW_SLOWDOWN | bench.Nvml.HW_THERMAL | bench.Nvml.SW_THERMAL)]
+    cs.lines = []
+    s = cs.summary()
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert s["sm_mhz"] == 1500.0
+
+
+def test_clock_sampler_without_nvidia_tools():
+    """Where neither nvidia-smi nor NVML exists (this CPU container), the
+    sampler records why and reports the region as unsampled."""
+    import bench
+    with bench.ClockSampler("GPU-none", poll_s=0.001) as cs:
+        pass
+    s = cs.summary()
+    if s["samples"] == 0:
+        assert s["reasons"] == ["unsampled"] and s["error"]
