@@ -925,11 +925,13 @@ def main():
                         "ms_per_step": round(f32["total_ms"] / K, 4),
                         "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in f32["kstats"].items()}}
     if not args.no_e2e and not args.profile_only:
-        e2e_ms, bi, bo = e2e_measure(wl, max(3, K // 2), 2, device)
-        ksteps = max(3, K // 2)
+        # at least 30 steps: the pipeline's first input copy and last result
+        # copy overlap nothing, and are spread over the steps like any other
+        ksteps = max(30, K)
+        e2e_ms, bi, bo = e2e_measure(wl, ksteps, 2, device)
         e2e_ms = max_over_ranks(dist, e2e_ms, device)
         line["e2e"] = {"value": round(world * wl.n * ksteps / (e2e_ms / 1e3), 1), "unit": UNIT,
-                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": ksteps}
     if not args.profile_only:
         bf = results = wl = None  # free the headline workload before the larger ones
         import torch
