@@ -23,9 +23,11 @@ __global__ void __launch_bounds__(kThreads) k_env_fill(const __grid_constant__ L
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
+  int lc = 0;  // the layer of g: g only grows, so its layer only advances
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int l = layer_of(cam, a.levels, g);
+    while (lc + 1 < a.levels && g >= cam.off[lc + 1]) ++lc;
+    const int l = lc;
     const int64_t p = g - cam.off[l];
     if (cam.cnt[l][p] != 0) continue;
     const int32_t wl = cam.w >> l, pi = (int32_t)p;  // a pyramid has fewer than 2^31 pixels
@@ -55,9 +57,11 @@ __global__ void __launch_bounds__(kThreads) k_env_grad(const __grid_constant__ L
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
+  int lc = 0;  // the layer of g: g only grows, so its layer only advances
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int l = layer_of(cam, a.levels, g);
+    while (lc + 1 < a.levels && g >= cam.off[lc + 1]) ++lc;
+    const int l = lc;
     const float* gl = cam.grad[l];
     const int64_t p = g - cam.off[l];
     if (gl == nullptr || cam.cnt[l][p] != 0) continue;

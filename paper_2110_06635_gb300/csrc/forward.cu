@@ -66,9 +66,11 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
+  int lc = 0;  // the layer of g: g only grows, so its layer only advances
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int l = layer_of(cam, a.levels, g);
+    while (lc + 1 < a.levels && g >= cam.off[lc + 1]) ++lc;
+    const int l = lc;
     const int64_t p = g - cam.off[l];
     cam.key[l][p] = ~0ull;
     cam.cnt[l][p] = 0u;
@@ -199,9 +201,11 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const __grid_constant__ 
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
+  int lc = 0;  // the layer of g: g only grows, so its layer only advances
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int l = layer_of(cam, a.levels, g);
+    while (lc + 1 < a.levels && g >= cam.off[lc + 1]) ++lc;
+    const int l = lc;
     TO* img = reinterpret_cast<TO*>(cam.image[l]);
     if (img == nullptr) continue;
     const int64_t p = g - cam.off[l];
