@@ -256,6 +256,15 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first
  *     call before any stream capture.
+ *   - Under lazy module loading (the CUDA default), the first adop_* call
+ *     on a device that launches a kernel loads the library's device code,
+ *     and that load places this array in device memory and may
+ *     synchronise.  Callers that must not allocate on their frame loop make
+ *     one warm-up call of this entry point outside it (or run with
+ *     CUDA_MODULE_LOADING=EAGER, which places the array when the context is
+ *     created).
+ *   - The looked-up address is kept for the life of the process: do not use
+ *     the library across a cudaDeviceReset of that device.
  *   - All calls share the array and it keeps the previous call's contents
  *     (every call overwrites what it reads).  Calls that overlap on the GPU
  *     (on different streams, or from different threads) race: serialise them.
@@ -268,6 +277,22 @@ adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_came
                                          const float* const* grad_image, float* grad_feat,
                                          float* grad_xyz, float* grad_pose, float* grad_intr,
                                          adop_stream stream);
+
+/*
+ * Tangent-space pose update (Sec. 3.1, implementation details, Eq. tangent):
+ * the pose is optimised through a tangent xi = (nu, omega) in se(3) that
+ * starts at zero; after each optimiser step the increment is applied as
+ * (R', t') = exp(xi) (R, t) and the tangent is reset.  For k < n:
+ * poses[k] <- exp(xi[6k .. 6k+5]) poses[k] (host memory, in place), with
+ * exp the closed-form SE(3) exponential:
+ *   E = I + a [omega]x + b [omega]x^2,  e = (I + b [omega]x + c [omega]x^2) nu,
+ *   a = sin(th)/th, b = (1 - cos(th))/th^2, c = (th - sin(th))/th^3,
+ *   th = |omega|;  R' = E R, t' = E t + e.
+ * Evaluated in FP64 from the FP32 pose and rounded to FP32 once.  Host only:
+ * no device memory, no stream.  ADOP_ERR_INVALID_ARG for n < 0, NULL
+ * pointers (n > 0) or a non-finite tangent (then no pose is changed).
+ */
+adop_status adop_pose_apply_tangent(const double* xi, adop_pose* poses, int32_t n);
 
 /* ------------------------------------------------------------------------
  * Render server: continuous batching of forward renders.

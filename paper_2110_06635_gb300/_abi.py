@@ -93,6 +93,7 @@ SIGNATURES = {
     "adop_atomic_probe": (ct.c_int, [ct.c_int32, _P, ct.c_int64, ct.c_int64, ct.c_uint64, _P]),
     "adop_profile_enable": (ct.c_int, [ct.c_int32]),
     "adop_profile_collect": (ct.c_int32, [_P, ct.c_int32]),
+    "adop_pose_apply_tangent": (ct.c_int, [_P, _P, ct.c_int32]),
 }
 
 
@@ -271,6 +272,17 @@ def _stream_ptr(stream):
     return ct.c_void_p(s.cuda_stream)
 
 
+def adop_pose_apply_tangent(xi, R, t):
+    """exp(xi) (R, t) for one pose (Eq. tangent), computed by the library:
+    xi = (nu, omega) (6 numbers), R (3 x 3) and t (3) -> (R', t') as float32
+    numpy arrays."""
+    x = np.ascontiguousarray(np.asarray(xi, np.float64).reshape(6))
+    pose = adop_pose((ct.c_float * 9)(*np.asarray(R, np.float32).reshape(9).tolist()),
+                     (ct.c_float * 3)(*np.asarray(t, np.float32).reshape(3).tolist()))
+    _check(load().adop_pose_apply_tangent(x.ctypes.data_as(ct.c_void_p), ct.byref(pose), 1))
+    return (np.array(pose.R[:], np.float32).reshape(3, 3), np.array(pose.t[:], np.float32))
+
+
 def adop_abi_version() -> int:
     return int(load().adop_abi_version())
 
@@ -336,11 +348,12 @@ def adop_photometric_backward(cams, params: Params, c: int, frames, grad_image0,
     grad_photo (n_cam x 9: ev, wb[3], vig_c[2], vig_a[3]) and grad_crf (the
     LUTs' gradients, camera after camera) from dL/d(layer-0 image)."""
     torch = _torch()
+    g1 = _grad_image_ptrs([[g] for g in grad_image0], cams, 1, c)
+    g0 = (ct.c_void_p * len(cams))(*[g1[k] for k in range(len(cams))])
     lib = load()
     pr = params.struct()
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
-    g0 = (ct.c_void_p * len(cams))(*[_dev_ptr(g) for g in grad_image0])
     nb = int(lib.adop_photometric_workspace_bytes(len(cams)))
     ws = torch.empty(nb + 256, dtype=torch.uint8, device=grad_photo.device)
     wp, wn = _ws_ptr(ws)
@@ -357,15 +370,35 @@ def adop_env_backward(cams, params: Params, c: int, frames, grad_images, grad_en
     """Gradient of the environment map params.env (Sec. 3.1), accumulated into
     grad_env (same shape) from grad_images[k][l] (dL/dI of camera k, layer l)
     at the pixels where no point landed."""
+    gi = _grad_image_ptrs(grad_images, cams, params.levels, c)
     lib = load()
     pr = params.struct()
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
-    L = params.levels
-    gi = (ct.c_void_p * (len(cams) * L))(*[_dev_ptr(g[l] if g is not None else None)
-                                          for g in grad_images for l in range(L)])
     _check(lib.adop_env_backward(arr, len(cams), ct.byref(pr), int(c), fr, gi, _dev_ptr(grad_env),
                                  _stream_ptr(stream)))
+
+
+def _grad_image_ptrs(grad_images, cams, levels: int, c: int):
+    """Pointer array grad_image[k * levels + l] of the backward entry points.
+    The kernels read each given gradient as c x h_l x w_l float32 values, so
+    anything else (another dtype, another size) is refused here, before any
+    launch."""
+    torch = _torch()
+    gptr = (ct.c_void_p * (len(cams) * levels))()
+    for k, cam in enumerate(cams):
+        row = grad_images[k] if grad_images is not None else None
+        for l in range(levels):
+            g = row[l] if row is not None else None
+            if g is None:
+                continue
+            if g.dtype != torch.float32:
+                raise ValueError(f"grad_images[{k}][{l}] must be float32, got {g.dtype}")
+            want = c * (int(cam.h) >> l) * (int(cam.w) >> l)
+            if g.numel() != want:
+                raise ValueError(f"grad_images[{k}][{l}] has {g.numel()} elements, c x h_l x w_l = {want} expected")
+            gptr[k * levels + l] = _dev_ptr(g)
+    return gptr
 
 
 def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):
@@ -383,18 +416,11 @@ def adop_render_backward(points: Points, cams, params: Params, frames, grad_imag
                          crf_luts=None):
     """Backward pass (Sec. 3.1).  grad_images[k][l]: dL/dI of camera k, layer l
     (float32 CUDA tensor c x h_l x w_l or None)."""
+    gptr = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
     lib = load()
     ps, pr = points.struct(), params.struct()
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
-    L = params.levels
-    gptr = (ct.c_void_p * (len(cams) * L))()
-    for k in range(len(cams)):
-        for l in range(L):
-            g = grad_images[k][l] if grad_images is not None and grad_images[k] is not None else None
-            if g is not None and g.dtype != _torch().float32:
-                raise ValueError("grad_images must be float32")
-            gptr[k * L + l] = _dev_ptr(g)
     wp, wn = _ws_ptr(workspace)
     _check(lib.adop_render_backward(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr, _dev_ptr(grad_feat),
                                     _dev_ptr(grad_xyz), _dev_ptr(grad_pose), _dev_ptr(grad_intr), wp, wn,
@@ -406,16 +432,11 @@ def adop_render_backward_noalloc(points: Points, cams, params: Params, frames, g
     """adop_render_backward without a workspace: the library's static scratch
     array is used instead (for callers that may not allocate device memory).
     Frames must carry the forward's kept state."""
+    gptr = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
     lib = load()
     ps, pr = points.struct(), params.struct()
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
-    L = params.levels
-    gptr = (ct.c_void_p * (len(cams) * L))()
-    for k in range(len(cams)):
-        for l in range(L):
-            g = grad_images[k][l] if grad_images is not None and grad_images[k] is not None else None
-            gptr[k * L + l] = _dev_ptr(g)
     _check(lib.adop_render_backward_noalloc(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr,
                                             _dev_ptr(grad_feat), _dev_ptr(grad_xyz), _dev_ptr(grad_pose),
                                             _dev_ptr(grad_intr), _stream_ptr(stream)))

@@ -22,14 +22,13 @@ per-point layer mask for the backward pass; ``keep_state=False`` keeps only
 the inputs and the backward pass re-renders the depth and accumulate passes
 (the paper's choice: Lambda is never stored).
 
-All arithmetic runs in the CUDA library; this module only allocates tensors
-and marshals pointers.  The pose exponential (6 numbers per camera) is
-evaluated on the host in FP64.
+All arithmetic runs in the library; this module only allocates tensors and
+marshals pointers.  The pose exponential (6 numbers per camera) is the
+library's host-side adop_pose_apply_tangent, in FP64.
 """
 from __future__ import annotations
 
 import copy
-import math
 
 import numpy as np
 import torch
@@ -37,39 +36,13 @@ import torch
 from . import _abi as A
 
 
-def se3_exp(xi) -> np.ndarray:
-    """4x4 SE(3) exponential of xi = (nu, omega) (closed form: Rodrigues for
-    the rotation, the left Jacobian for the translation)."""
-    xi = np.asarray(xi, np.float64)
-    nu, om = xi[:3], xi[3:]
-    th = float(np.linalg.norm(om))
-    K = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
-    if th < 1e-8:
-        R = np.eye(3) + K + 0.5 * K @ K
-        V = np.eye(3) + 0.5 * K + K @ K / 6.0
-    else:
-        a = math.sin(th) / th
-        b = (1 - math.cos(th)) / th ** 2
-        c = (th - math.sin(th)) / th ** 3
-        R = np.eye(3) + a * K + b * K @ K
-        V = np.eye(3) + b * K + c * K @ K
-    T = np.eye(4)
-    T[:3, :3] = R
-    T[:3, 3] = V @ nu
-    return T
-
-
 def apply_tangent(cam, xi):
     """The camera with its pose replaced by exp(xi) (R, t) (Eq. tangent): the
     update applied after an optimiser step on the tangent, which is then
-    reset to zero."""
-    T = np.eye(4)
-    T[:3, :3] = np.asarray(cam.R, np.float64)
-    T[:3, 3] = np.asarray(cam.t, np.float64)
-    T = se3_exp(np.asarray(xi, np.float64)) @ T
+    reset to zero.  The exponential and the composition run in the library
+    (adop_pose_apply_tangent)."""
     c = copy.copy(cam)
-    c.R = T[:3, :3].astype(np.float32)
-    c.t = T[:3, 3].astype(np.float32)
+    c.R, c.t = A.adop_pose_apply_tangent(xi, cam.R, cam.t)
     return c
 
 

@@ -139,3 +139,26 @@ def test_env_backward_validates(lib):
     # frames without the forward's counts
     st = so.adop_env_backward(cam, 1, ct.byref(prm), 8, fr, None, g, None)
     assert st == 1 and "count" in so.adop_last_error().decode()
+
+
+@pytest.mark.parametrize("entry", ["adop_render_backward", "adop_render_backward_noalloc"])
+def test_grad_images_checked_before_launch(lib, entry):
+    """Both backward wrappers read every upstream gradient as c x h_l x w_l
+    float32 values: another dtype or size is refused on the host (the tensors
+    here are CPU tensors, so nothing could have been launched)."""
+    import numpy as np
+    import torch
+    import scenes
+    adop, _ = lib
+    cam = scenes.Camera(64, 48, 50.0, 50.0, 32.0, 24.0, R=np.eye(3, dtype=np.float32),
+                        t=np.array([0, 0, 2], np.float32))
+    pts = adop.Points(torch.zeros((10, 3)), torch.zeros((10, 4)))
+    params = adop.Params(2, 0.01, 1e-3, None, 0)
+    fn = getattr(adop, entry)
+    extra = [None] * 4 + ([torch.zeros(1)] if entry == "adop_render_backward" else [])
+    bad_dtype = [[torch.zeros((4, 48, 64), dtype=torch.bfloat16), None]]
+    with pytest.raises(ValueError, match="float32"):
+        fn(pts, [cam], params, [None], bad_dtype, *extra)
+    bad_size = [[None, torch.zeros((4, 24, 31))]]
+    with pytest.raises(ValueError, match="elements"):
+        fn(pts, [cam], params, [None], bad_size, *extra)

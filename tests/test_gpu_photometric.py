@@ -71,7 +71,7 @@ def test_pose_recovery_through_the_tangent(adop):
     Adam steps on the tangent xi (applied and reset each step, as in the
     paper); the one-pixel spatial gradient must pull the pose back."""
     import torch
-    from paper_2110_06635_gb300.autograd import apply_tangent, rasterize, se3_exp
+    from paper_2110_06635_gb300.autograd import apply_tangent, rasterize
     sc = scenes.tiny_spheres(40000, 4, seed=77)
     p = sc.xyz.astype(np.float64)
     sc.feat = np.stack([np.sin(4 * p[:, 0]), np.cos(4 * p[:, 1]), np.sin(4 * p[:, 2] + 1), np.cos(3 * p[:, 0] + 2 * p[:, 1])],

@@ -5,16 +5,18 @@ application that owns all device memory through its own pool and forbids
 allocations on its frame loop (an allocation can synchronise the device and
 stall a frame), or a process whose device-memory budget is fixed up front.
 For them the library keeps its backward scratch in one static device array.
-This test calls that entry point through the C ABI twice in a row and checks
+The tests call that entry point through the C ABI twice in a row and check
 each result against the workspace-taking adop_render_backward on the same
-inputs, within the tolerances of the parity tests.  It lives in a file of its
-own that is collected last, and it needs no state from other tests.
+inputs, and against the FP64 CPU oracle directly, within the tolerances of
+the parity tests; and they check the defining property -- one call after a
+warm-up leaves the device's free memory unchanged.  They live in a file of
+their own that is collected last, and need no state from other tests.
 """
 import numpy as np
 import pytest
 
 import scenes
-from parity import RTOL_GRAD, assert_close, assert_reduced
+from parity import RTOL_GRAD, assert_close, assert_reduced, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -79,3 +81,39 @@ def test_noalloc_rejects_what_does_not_fit(adop):
     stateless = [adop.Frame.alloc(big, 8, 4, torch.float32, False, "cuda")]
     with pytest.raises(adop.AdopError, match="kept key/count/acc"):
         adop.adop_render_backward_noalloc(pts, [big], params, stateless, G)
+
+
+def test_noalloc_backward_matches_the_oracle(adop, orc):
+    """Against the FP64 oracle itself: per-point gradients within 1e-4 of
+    max(|ref|, rms), pose and intrinsics within 1e-4 of the summed absolute
+    (point, layer) terms."""
+    sc = scenes.tiny_spheres(20000, 4, seed=1001)
+    cams = [scenes.tiny_camera()]
+    pts, params, frames, ws, G = _setup(adop, sc, cams)
+    Gh = [[g.cpu().numpy() for g in row] for row in G]
+    r = oracle_run(orc, sc, cams, "f32", grads=Gh)
+    for _ in range(2):
+        got = _grads(adop, sc, cams, pts, params, frames, G)
+        assert_close(got[0], r["dfeat"], RTOL_GRAD, "dL/dtau vs oracle")
+        assert_close(got[1], r["dxyz"], RTOL_GRAD, "dL/dx vs oracle")
+        assert_reduced(got[2][0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi vs oracle")
+        assert_reduced(got[3][0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK vs oracle")
+
+
+def test_noalloc_call_allocates_no_device_memory(adop):
+    """After one warm-up call (which may load the library's device code and
+    place the static array), a further call leaves cudaMemGetInfo's free
+    bytes unchanged."""
+    import torch
+    sc = scenes.tiny_spheres(20000, 4, seed=1001)
+    cams = [scenes.tiny_camera()]
+    pts, params, frames, ws, G = _setup(adop, sc, cams)
+    out = [torch.zeros((sc.n, sc.c), device="cuda"), torch.zeros((sc.n, 3), device="cuda"),
+           torch.zeros((1, 6), device="cuda"), torch.zeros((1, 6), device="cuda")]
+    adop.adop_render_backward_noalloc(pts, cams, params, frames, G, *out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    adop.adop_render_backward_noalloc(pts, cams, params, frames, G, *out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
