@@ -28,13 +28,21 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
+GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fno-math-errno",
+             "-Wall"]
+
+
 def build(force: bool = False) -> str:
-    """Compile the C oracle into ``oracle/liboracle.so`` (gcc, no FMA contraction)."""
+    """Compile the C oracle into ``oracle/liboracle.so`` (gcc, no FMA
+    contraction), with OpenMP where the compiler has it (threads are a timing
+    aid only: the results do not depend on them), else without."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-             "-fno-math-errno", "-Wall", "-o", tmp, _SRC, "-lm"])
+        try:
+            subprocess.check_call(["gcc", *GCC_FLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -64,7 +72,9 @@ def _load():
         lib.orc_pyramid_pixels.restype = ct.c_int64
         lib.orc_forward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P, ct.c_int32, ct.c_float,
                                     ct.c_float, _P, _P, _P, ct.c_float, ct.c_int32, _P, ct.c_int32, ct.c_int32,
-                                    _P, _P, _P, _P, _P]
+                                    _P, _P, _P, _P, _P, ct.c_int32]
+        lib.orc_threads.argtypes = [ct.c_int32]
+        lib.orc_threads.restype = ct.c_int32
         lib.orc_camera_inverse_f64.argtypes = [_P, ct.c_double, ct.c_double, _P]
         lib.orc_env_sample.argtypes = [_P, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P, _P]
         lib.orc_env_grad.argtypes = [_P, _P, ct.c_int32, ct.c_int32, _P, _P, ct.c_int32, ct.c_int32, _P]
@@ -75,7 +85,7 @@ def _load():
         lib.orc_camera_f64_many.argtypes = [ct.c_int64, _P, _P, _P, ct.c_int32]
         lib.orc_backward.argtypes = [ct.c_int64, _P, ct.c_int32, _P, _P, _P, ct.c_int32, ct.c_float,
                                      _P, ct.c_int32, ct.c_int32, _P, _P, _P, _P, _P, _P,
-                                     _P, _P, _P, _P, _P, _P, _P, _P]
+                                     _P, _P, _P, _P, _P, _P, _P, _P, _P, ct.c_int64, ct.c_int32]
         lib.orc_backward.restype = ct.c_int
         lib.orc_epilogue.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_double, _P, _P, _P,
                                      _P, ct.c_int32, ct.c_int32, _P]
@@ -217,10 +227,16 @@ def knn_radius(xyz, k: int = 4) -> np.ndarray:
     return out
 
 
+def threads(requested: int = 0) -> int:
+    """Threads a request gets (0: every core; 1 without OpenMP)."""
+    return int(_load().orc_threads(int(requested)))
+
+
 def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, normals=None,
-            radius=None, beta=None, gamma=1.5, log_desc=False, env=None) -> Forward:
+            radius=None, beta=None, gamma=1.5, log_desc=False, env=None, threads=1) -> Forward:
     """One camera through Sec. 3.1's forward pass (Eq. render ... Eq. blend);
-    with radius/beta, stochastic point discarding (Eq. discard) at every layer."""
+    with radius/beta, stochastic point discarding (Eq. discard) at every layer.
+    threads (0 = every core) changes the time, not the result."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
     f64 = np.ascontiguousarray(feat_to_f64(feat))
@@ -241,13 +257,14 @@ def forward(xyz, feat, cam, levels=4, alpha=0.01, znear=1e-3, background=None, n
     eh, ew = (0, 0) if env is None else E.shape[1:]
     rc = lib.orc_forward(n, _ptr(xyz), c, _ptr(f64), _ptr(nrm), ct.byref(K), ct.byref(T), int(levels),
                          ct.c_float(alpha), ct.c_float(znear), _ptr(bg), _ptr(rad), _ptr(bet), ct.c_float(gamma),
-                         int(bool(log_desc)), _ptr(E), ew, eh, _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
+                         int(bool(log_desc)), _ptr(E), ew, eh, _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z),
+                         int(threads))
     if rc != 0:
         raise MemoryError("oracle forward: allocation failed")
     return Forward(keys, cnt, img, pix, z, int(cam.w), int(cam.h), int(levels), c)
 
 
-def keys_counts(xyz, cam, levels=4, alpha=0.01, znear=1e-3) -> Forward:
+def keys_counts(xyz, cam, levels=4, alpha=0.01, znear=1e-3, threads=1) -> Forward:
     """Sec. 3.1's forward without descriptors: every point's pixel per layer
     and depth (Eq. render ... Eq. boundscheck), the nearest-depth keys and the
     fuzzy-test counts |Lambda| (Eq. depthtest) -- for clouds too large to
@@ -264,7 +281,7 @@ def keys_counts(xyz, cam, levels=4, alpha=0.01, znear=1e-3) -> Forward:
     K, T = _intr(cam), _pose(cam)
     rc = lib.orc_forward(n, _ptr(xyz), 0, None, None, ct.byref(K), ct.byref(T), int(levels), ct.c_float(alpha),
                          ct.c_float(znear), None, None, None, ct.c_float(1.5), 0, None, 0, 0,
-                         _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z))
+                         _ptr(keys), _ptr(cnt), _ptr(img), _ptr(pix), _ptr(z), int(threads))
     if rc != 0:
         raise MemoryError("oracle forward: allocation failed")
     return Forward(keys, cnt, img[:0], pix, z, int(cam.w), int(cam.h), int(levels), 0)
@@ -314,9 +331,12 @@ class Backward:
 
 
 def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_projected=False,
-             log_desc=False) -> Backward:
+             log_desc=False, threads=1, sample=None) -> Backward:
     """Sec. 3.1's backward pass for one camera; G is dL/dI over the
-    concatenated pyramid (same layout as ``fwd.img``)."""
+    concatenated pyramid (same layout as ``fwd.img``).  sample: point indices
+    to visit (None = all): only their rows are written and only their terms
+    are summed into the pose and intrinsics gradients.  threads (0 = every
+    core) changes the time; only the reduced sums' FP64 rounding may follow it."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
     f64 = np.ascontiguousarray(feat_to_f64(feat))
@@ -329,12 +349,15 @@ def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_p
     gu = np.empty((n, fwd.levels))
     gv = np.empty((n, fwd.levels))
     bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
+    smp = None if sample is None else np.ascontiguousarray(sample, dtype=np.int64)
+    if smp is not None and smp.size and (smp.min() < 0 or smp.max() >= n):
+        raise IndexError("sample index outside [0, n)")
     K, T = _intr(cam), _pose(cam)
     rc = lib.orc_backward(n, _ptr(xyz), c, _ptr(f64), ct.byref(K), ct.byref(T), fwd.levels,
                           ct.c_float(alpha), _ptr(bg), int(bool(all_projected)), int(bool(log_desc)), _ptr(fwd.keys),
                           _ptr(fwd.cnt), _ptr(fwd.img), _ptr(fwd.pix), _ptr(fwd.z), _ptr(G),
                           _ptr(dfeat), _ptr(dxyz), _ptr(dpose), _ptr(dintr), _ptr(dpa), _ptr(dia),
-                          _ptr(gu), _ptr(gv))
+                          _ptr(gu), _ptr(gv), _ptr(smp), 0 if smp is None else smp.size, int(threads))
     if rc != 0:
         raise MemoryError("oracle backward: allocation failed")
     return Backward(dfeat, dxyz, dpose, dintr, dpa, dia, gu, gv)

@@ -42,6 +42,44 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Threads (a timing aid only: results do not depend on them, see the    */
+/* forward and backward below)                                           */
+/* ------------------------------------------------------------------ */
+
+/* Threads to use for a request of `threads` (<= 0: every core; 1 when the
+ * library was built without OpenMP). */
+static int team_size(int32_t threads) {
+#ifdef _OPENMP
+    return threads > 0 ? threads : omp_get_num_procs();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
+static int thread_id(void) {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+static int threads_in_team(void) {
+#ifdef _OPENMP
+    return omp_get_num_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Threads a request of `threads` gets (exported for the timing legs). */
+int32_t orc_threads(int32_t threads) { return team_size(threads); }
 
 /* Camera model C.  model 0: pinhole with Brown-Conrady distortion (k1,k2,k3
  * radial, p1,p2 tangential); the paper's scenes use "Pinhole + Dist." (Table
@@ -188,7 +226,9 @@ static int discard_keep(const orc_intrinsics* K, float z, float r, float beta, f
 static void project_all(int64_t n, const float* xyz, const float* normals,
                         const orc_intrinsics* K, const orc_pose* T, int levels, float znear,
                         const float* radius, const float* beta, float gamma,
-                        int32_t* pix, float* zf) {
+                        int32_t* pix, float* zf, int nt) {
+    /* every point on its own: any split over threads gives the same arrays */
+#pragma omp parallel for schedule(static) num_threads(nt)
     for (int64_t i = 0; i < n; ++i) {
         float X[3], u0 = 0.0f, v0 = 0.0f, z;
         transform_f32(T, xyz + 3 * i, X);
@@ -352,6 +392,8 @@ void orc_env_grad(const orc_intrinsics* K, const orc_pose* T, int32_t levels, in
  * Outputs (all over the concatenated pyramid of `levels` layers):
  *   keys  uint64 per pixel; cnt  |Lambda| per pixel; img  c x h_l x w_l;
  *   pix   n x levels pixel id or -1 (may be NULL); zf  n depths (may be NULL).
+ * threads: threads to use (<= 0: every core); the results are the same for
+ *   any value (see the steps below).
  * Returns 0, or -1 if an allocation fails.
  */
 int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, const float* normals,
@@ -359,14 +401,17 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
                 float znear, const double* background,
                 const float* radius, const float* beta, float gamma, int32_t log_desc,
                 const double* env, int32_t env_w, int32_t env_h,
-                uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out) {
+                uint64_t* keys, uint32_t* cnt, double* img, int32_t* pix_out, float* z_out,
+                int32_t threads) {
     int64_t npx = orc_pyramid_pixels(K->w, K->h, levels);
+    const int nt = team_size(threads);
     /* Logarithmic descriptors (Sec. 3.2) are converted to linear values before
      * blending. */
     double* lin = NULL;
     if (log_desc) {
         lin = (double*)malloc(sizeof(double) * (size_t)(n * c + 1));
         if (!lin) return -1;
+#pragma omp parallel for schedule(static) num_threads(nt)
         for (int64_t j = 0; j < n * c; ++j) lin[j] = exp(feat[j]);
         feat = lin;
     }
@@ -377,65 +422,90 @@ int orc_forward(int64_t n, const float* xyz, int32_t c, const double* feat, cons
 
     /* Step 1: project every point to every layer (Eqs. projection, round,
      * boundscheck, normalculling). */
-    project_all(n, xyz, normals, K, T, levels, znear, radius, beta, gamma, pix, zf);
+    project_all(n, xyz, normals, K, T, levels, znear, radius, beta, gamma, pix, zf, nt);
 
-    /* Step 2: nearest depth per pixel, as a (depth bits, index) key so that
-     * equal depths resolve to the smallest point index. */
-    for (int64_t p = 0; p < npx; ++p) keys[p] = UINT64_MAX;
-    for (int l = 0; l < levels; ++l) {
-        int64_t off = layer_offset(K->w, K->h, l);
-        for (int64_t i = 0; i < n; ++i) {
-            int32_t p = pix[i * levels + l];
-            if (p < 0) continue;
-            uint64_t key = ((uint64_t)f32_bits(zf[i]) << 32) | (uint64_t)(uint32_t)i;
-            if (key < keys[off + p]) keys[off + p] = key;
-        }
-    }
-
-    /* Step 3: fuzzy depth test (Eq. depthtest) against min_z(p), taken in
-     * FP32: pass iff z <= f32(min_z * f32(1 + alpha)).  Step 4: Lambda's
-     * size and the feature sum, for the mean of Eq. blend. */
+    /* Steps 2-4 visit the (point, layer) pairs in point-index order, layer by
+     * layer.  With several threads, each thread owns one contiguous range
+     * [g0, g1) of the pyramid's pixels and takes only the pairs that land
+     * there, still in that order: every pixel then sees exactly the same
+     * sequence of updates as with one thread, so keys, counts and the FP64
+     * sums do not depend on the thread count. */
     const float a1 = 1.0f + alpha;
-    for (int64_t p = 0; p < npx; ++p) cnt[p] = 0;
-    for (int l = 0; l < levels; ++l) {
-        int64_t off = layer_offset(K->w, K->h, l);
-        for (int64_t i = 0; i < n; ++i) {
-            int32_t p = pix[i * levels + l];
-            if (p < 0) continue;
-            float minz = bits_f32((uint32_t)(keys[off + p] >> 32));
-            float thr = minz * a1;
-            if (!(zf[i] <= thr)) continue;
-            cnt[off + p] += 1;
-            for (int ch = 0; ch < c; ++ch) sum[(off + p) * c + ch] += feat[i * c + ch];
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = thread_id(), tt = threads_in_team();
+        const int64_t g0 = npx * t / tt, g1 = npx * (t + 1) / tt;
+
+        /* Step 2: nearest depth per pixel, as a (depth bits, index) key so
+         * that equal depths resolve to the smallest point index. */
+        for (int64_t g = g0; g < g1; ++g) keys[g] = UINT64_MAX;
+        for (int l = 0; l < levels; ++l) {
+            int64_t off = layer_offset(K->w, K->h, l);
+            for (int64_t i = 0; i < n; ++i) {
+                int32_t p = pix[i * levels + l];
+                if (p < 0 || off + p < g0 || off + p >= g1) continue;
+                uint64_t key = ((uint64_t)f32_bits(zf[i]) << 32) | (uint64_t)(uint32_t)i;
+                if (key < keys[off + p]) keys[off + p] = key;
+            }
+        }
+
+        /* Step 3: fuzzy depth test (Eq. depthtest) against min_z(p), taken
+         * in FP32: pass iff z <= f32(min_z * f32(1 + alpha)).  Step 4:
+         * Lambda's size and the feature sum, for the mean of Eq. blend. */
+        for (int64_t g = g0; g < g1; ++g) cnt[g] = 0;
+        for (int l = 0; l < levels; ++l) {
+            int64_t off = layer_offset(K->w, K->h, l);
+            for (int64_t i = 0; i < n; ++i) {
+                int32_t p = pix[i * levels + l];
+                if (p < 0 || off + p < g0 || off + p >= g1) continue;
+                float minz = bits_f32((uint32_t)(keys[off + p] >> 32));
+                float thr = minz * a1;
+                if (!(zf[i] <= thr)) continue;
+                cnt[off + p] += 1;
+                for (int ch = 0; ch < c; ++ch) sum[(off + p) * c + ch] += feat[i * c + ch];
+            }
         }
     }
 
     /* Step 5: Eq. blend -- the mean over Lambda, or, for an empty pixel, the
-     * environment map E(R^T C^-1(u, v)) (or the constant background). */
-    double* ev = (double*)malloc(sizeof(double) * (size_t)(c + 1));
-    if (!ev) return -1;
+     * environment map E(R^T C^-1(u, v)) (or the constant background).  Every
+     * pixel on its own. */
+    int failed = 0;
     for (int l = 0; l < levels; ++l) {
         int64_t off = layer_offset(K->w, K->h, l);
         const int32_t wl = K->w >> l;
         int64_t np = (int64_t)wl * (K->h >> l);
-        for (int64_t p = 0; p < np; ++p) {
-            if (cnt[off + p] == 0 && env) {
-                double dw[3];
-                pixel_ray(K, T, l, (int32_t)(p % wl), (int32_t)(p / wl), dw);
-                orc_env_sample(env, c, env_w, env_h, dw, ev, NULL, NULL);
+#pragma omp parallel num_threads(nt) reduction(| : failed)
+        {
+            double* ev = (double*)malloc(sizeof(double) * (size_t)(c + 1));
+            if (!ev) failed = 1;
+#pragma omp for schedule(static)
+            for (int64_t p = 0; p < np; ++p) {
+                if (!ev) continue;
+                if (cnt[off + p] == 0 && env) {
+                    double dw[3];
+                    pixel_ray(K, T, l, (int32_t)(p % wl), (int32_t)(p / wl), dw);
+                    orc_env_sample(env, c, env_w, env_h, dw, ev, NULL, NULL);
+                }
+                for (int ch = 0; ch < c; ++ch) {
+                    double v;
+                    if (cnt[off + p] == 0)
+                        v = env ? ev[ch] : (background ? background[ch] : 0.0);
+                    else
+                        v = sum[(off + p) * c + ch] / (double)cnt[off + p];
+                    img[c * off + (int64_t)ch * np + p] = v;
+                }
             }
-            for (int ch = 0; ch < c; ++ch) {
-                double v;
-                if (cnt[off + p] == 0)
-                    v = env ? ev[ch] : (background ? background[ch] : 0.0);
-                else
-                    v = sum[(off + p) * c + ch] / (double)cnt[off + p];
-                img[c * off + (int64_t)ch * np + p] = v;
-            }
+            free(ev);
         }
     }
-    free(ev);
     free(sum);
+    if (failed) {
+        free(lin);
+        if (!pix_out) free(pix);
+        if (!z_out) free(zf);
+        return -1;
+    }
     free(lin);
     if (!pix_out) free(pix);
     if (!z_out) free(zf);
@@ -577,6 +647,13 @@ void orc_project_jac_f64(const orc_intrinsics* K, const orc_pose* T, const float
  *   dintr 6        dL/d(fx, fy, cx, cy, k1, k2)
  *   dpose_abs, dintr_abs  sum of |per (point, layer) term| (error scale)
  *   gu, gv  n x levels   the layer-pixel gradients g_u, g_v (may be NULL)
+ * sample (NULL = every point): n_sample point indices to visit instead of all
+ *   n; the other rows stay zero and the reduced sums cover the sample only.
+ *   It restricts which points are visited, not what is computed for one.
+ * threads: as in orc_forward.  Per-point outputs do not depend on it; the
+ *   reduced sums are added per thread, then over the threads in order, so
+ *   with more than one thread they may differ from one thread's in FP64
+ *   rounding.
  *
  * Induced change D at a target pixel q one pixel away (Eq. spatialderiv,
  * read with the conditions on the target q):
@@ -596,15 +673,16 @@ int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
                  const uint64_t* keys, const uint32_t* cnt, const double* img,
                  const int32_t* pix, const float* zf, const double* G,
                  double* dfeat, double* dxyz, double* dpose, double* dintr,
-                 double* dpose_abs, double* dintr_abs, double* gu_out, double* gv_out) {
+                 double* dpose_abs, double* dintr_abs, double* gu_out, double* gv_out,
+                 const int64_t* sample, int64_t n_sample, int32_t threads) {
     const float a1 = 1.0f + alpha;
-    double* D = (double*)malloc(sizeof(double) * (size_t)(c > 0 ? c : 1));
-    if (!D) return -1;
+    const int nt = team_size(threads);
     const double* feat_stored = feat;
     double* lin = NULL;
     if (log_desc) { /* blend and induced changes act on exp(tau) (Sec. 3.2) */
         lin = (double*)malloc(sizeof(double) * (size_t)(n * c + 1));
         if (!lin) return -1;
+#pragma omp parallel for schedule(static) num_threads(nt)
         for (int64_t j = 0; j < n * c; ++j) lin[j] = exp(feat_stored[j]);
         feat = lin;
     }
@@ -614,110 +692,140 @@ int orc_backward(int64_t n, const float* xyz, int32_t c, const double* feat,
     if (gu_out)
         for (int64_t i = 0; i < n * levels; ++i) gu_out[i] = gv_out[i] = 0.0;
 
-    for (int64_t i = 0; i < n; ++i) {
-        const double* tau = feat + i * c;
-        double dL_du0 = 0.0, dL_dv0 = 0.0;
-        double tu[8], tv[8]; /* per layer contributions to du0, dv0 */
-        for (int l = 0; l < levels; ++l) {
-            tu[l] = tv[l] = 0.0;
-            int32_t p = pix[i * levels + l];
-            if (p < 0) continue;
-            const int32_t wl = K->w >> l, hl = K->h >> l;
-            const int64_t np = (int64_t)wl * hl;
-            const int64_t off = layer_offset(K->w, K->h, l);
-            const double* Il = img + c * off;
-            const double* Gl = G + c * off;
-            float minz_p = bits_f32((uint32_t)(keys[off + p] >> 32));
-            int in_lambda = (zf[i] <= minz_p * a1);
-
-            /* Feature gradient: d mean / d tau_i = 1/|Lambda| for members. */
-            if (in_lambda)
-                for (int ch = 0; ch < c; ++ch)
-                    dfeat[i * c + ch] += Gl[(int64_t)ch * np + p] / (double)cnt[off + p];
-
-            if (!in_lambda && !all_projected) continue;
-            const int32_t pu = p % wl, pv = p / wl;
-            const int32_t du[4] = {+1, -1, 0, 0};
-            const int32_t dv[4] = {0, 0, +1, -1};
-            double contrib[4];
-            for (int s = 0; s < 4; ++s) {
-                contrib[s] = 0.0;
-                int32_t qu = pu + du[s], qv = pv + dv[s];
-                if (qu < 0 || qu >= wl || qv < 0 || qv >= hl) continue;
-                int64_t q = (int64_t)qv * wl + qu;
-                uint32_t nq = cnt[off + q];
-                float minz_q = bits_f32((uint32_t)(keys[off + q] >> 32));
-                for (int ch = 0; ch < c; ++ch) {
-                    double Iq = Il[(int64_t)ch * np + q];
-                    if (nq == 0)
-                        D[ch] = tau[ch] - Iq; /* background overwritten */
-                    else if (zf[i] > minz_q * a1)
-                        D[ch] = 0.0; /* behind the target's surface */
-                    else if (zf[i] * a1 < minz_q)
-                        D[ch] = tau[ch] - Iq; /* in front: replaces the mean */
-                    else
-                        D[ch] = ((double)nq * Iq + tau[ch]) / (1.0 + (double)nq) - Iq;
-                }
-                double dot = 0.0;
-                for (int ch = 0; ch < c; ++ch) dot += Gl[(int64_t)ch * np + q] * D[ch];
-                contrib[s] = dot;
-            }
-            double g_u = 0.5 * (contrib[0] - contrib[1]);
-            double g_v = 0.5 * (contrib[2] - contrib[3]);
-            if (gu_out) {
-                gu_out[i * levels + l] = g_u;
-                gv_out[i * levels + l] = g_v;
-            }
-            double sc = ldexp(1.0, -l);
-            tu[l] = g_u * sc;
-            tv[l] = g_v * sc;
-            dL_du0 += tu[l];
-            dL_dv0 += tv[l];
-        }
-        if (dL_du0 == 0.0 && dL_dv0 == 0.0) {
-            int any = 0;
-            for (int l = 0; l < levels; ++l) any |= (tu[l] != 0.0 || tv[l] != 0.0);
-            if (!any) continue;
-        }
-        double uv[2], X[3], J_X[6], J_K[12];
-        orc_project_jac_f64(K, T, xyz + 3 * i, uv, X, J_X, J_K);
-        double dX[3];
-        for (int k = 0; k < 3; ++k) dX[k] = J_X[k] * dL_du0 + J_X[3 + k] * dL_dv0;
-        /* dL/dx = R^T dL/dX */
-        for (int k = 0; k < 3; ++k)
-            dxyz[i * 3 + k] = (double)T->R[0 * 3 + k] * dX[0] + (double)T->R[1 * 3 + k] * dX[1] +
-                              (double)T->R[2 * 3 + k] * dX[2];
-        /* Left increment exp(xi)(R,t): X' = X + nu + omega x X, so
-         * dL/dnu = dL/dX and dL/domega = X x dL/dX. */
-        double dxi[6] = {dX[0], dX[1], dX[2],
-                         X[1] * dX[2] - X[2] * dX[1],
-                         X[2] * dX[0] - X[0] * dX[2],
-                         X[0] * dX[1] - X[1] * dX[0]};
-        for (int k = 0; k < 6; ++k) {
-            dpose[k] += dxi[k];
-            double dk = J_K[k] * dL_du0 + J_K[6 + k] * dL_dv0;
-            dintr[k] += dk;
-        }
-        /* error scale: sum of the magnitudes of each layer's own term */
-        for (int l = 0; l < levels; ++l) {
-            if (tu[l] == 0.0 && tv[l] == 0.0) continue;
-            double eX[3];
-            for (int k = 0; k < 3; ++k) eX[k] = J_X[k] * tu[l] + J_X[3 + k] * tv[l];
-            double exi[6] = {eX[0], eX[1], eX[2],
-                             X[1] * eX[2] - X[2] * eX[1],
-                             X[2] * eX[0] - X[0] * eX[2],
-                             X[0] * eX[1] - X[1] * eX[0]};
-            for (int k = 0; k < 6; ++k) {
-                dpose_abs[k] += fabs(exi[k]);
-                dintr_abs[k] += fabs(J_K[k] * tu[l] + J_K[6 + k] * tv[l]);
-            }
-        }
+    /* The points visited: all of them in index order, or the given sample
+     * (point indices; only their rows of dfeat, dxyz, gu, gv are written and
+     * only their terms enter the reduced sums).  Every point's own outputs
+     * depend on nothing but its own terms; the reduced sums (pose,
+     * intrinsics) are summed point by point within each thread's contiguous
+     * share of the list, then over the threads in order. */
+    const int64_t m = sample ? n_sample : n;
+    double* part = (double*)calloc((size_t)nt * 24, sizeof(double));
+    if (!part) {
+        free(lin);
+        return -1;
     }
+    int failed = 0;
+#pragma omp parallel num_threads(nt) reduction(| : failed)
+    {
+        const int t = thread_id(), tt = threads_in_team();
+        const int64_t j0 = m * t / tt, j1 = m * (t + 1) / tt;
+        double* acc = part + 24 * t; /* dpose, dintr, dpose_abs, dintr_abs */
+        double* D = (double*)malloc(sizeof(double) * (size_t)(c > 0 ? c : 1));
+        if (!D) failed = 1;
+        for (int64_t j = j0; D && j < j1; ++j) {
+            const int64_t i = sample ? sample[j] : j;
+            const double* tau = feat + i * c;
+            double dL_du0 = 0.0, dL_dv0 = 0.0;
+            double tu[8], tv[8]; /* per layer contributions to du0, dv0 */
+            for (int l = 0; l < levels; ++l) {
+                tu[l] = tv[l] = 0.0;
+                int32_t p = pix[i * levels + l];
+                if (p < 0) continue;
+                const int32_t wl = K->w >> l, hl = K->h >> l;
+                const int64_t np = (int64_t)wl * hl;
+                const int64_t off = layer_offset(K->w, K->h, l);
+                const double* Il = img + c * off;
+                const double* Gl = G + c * off;
+                float minz_p = bits_f32((uint32_t)(keys[off + p] >> 32));
+                int in_lambda = (zf[i] <= minz_p * a1);
+
+                /* Feature gradient: d mean / d tau_i = 1/|Lambda| for members. */
+                if (in_lambda)
+                    for (int ch = 0; ch < c; ++ch)
+                        dfeat[i * c + ch] += Gl[(int64_t)ch * np + p] / (double)cnt[off + p];
+
+                if (!in_lambda && !all_projected) continue;
+                const int32_t pu = p % wl, pv = p / wl;
+                const int32_t du[4] = {+1, -1, 0, 0};
+                const int32_t dv[4] = {0, 0, +1, -1};
+                double contrib[4];
+                for (int s = 0; s < 4; ++s) {
+                    contrib[s] = 0.0;
+                    int32_t qu = pu + du[s], qv = pv + dv[s];
+                    if (qu < 0 || qu >= wl || qv < 0 || qv >= hl) continue;
+                    int64_t q = (int64_t)qv * wl + qu;
+                    uint32_t nq = cnt[off + q];
+                    float minz_q = bits_f32((uint32_t)(keys[off + q] >> 32));
+                    for (int ch = 0; ch < c; ++ch) {
+                        double Iq = Il[(int64_t)ch * np + q];
+                        if (nq == 0)
+                            D[ch] = tau[ch] - Iq; /* background overwritten */
+                        else if (zf[i] > minz_q * a1)
+                            D[ch] = 0.0; /* behind the target's surface */
+                        else if (zf[i] * a1 < minz_q)
+                            D[ch] = tau[ch] - Iq; /* in front: replaces the mean */
+                        else
+                            D[ch] = ((double)nq * Iq + tau[ch]) / (1.0 + (double)nq) - Iq;
+                    }
+                    double dot = 0.0;
+                    for (int ch = 0; ch < c; ++ch) dot += Gl[(int64_t)ch * np + q] * D[ch];
+                    contrib[s] = dot;
+                }
+                double g_u = 0.5 * (contrib[0] - contrib[1]);
+                double g_v = 0.5 * (contrib[2] - contrib[3]);
+                if (gu_out) {
+                    gu_out[i * levels + l] = g_u;
+                    gv_out[i * levels + l] = g_v;
+                }
+                double sc = ldexp(1.0, -l);
+                tu[l] = g_u * sc;
+                tv[l] = g_v * sc;
+                dL_du0 += tu[l];
+                dL_dv0 += tv[l];
+            }
+            if (dL_du0 == 0.0 && dL_dv0 == 0.0) {
+                int any = 0;
+                for (int l = 0; l < levels; ++l) any |= (tu[l] != 0.0 || tv[l] != 0.0);
+                if (!any) continue;
+            }
+            double uv[2], X[3], J_X[6], J_K[12];
+            orc_project_jac_f64(K, T, xyz + 3 * i, uv, X, J_X, J_K);
+            double dX[3];
+            for (int k = 0; k < 3; ++k) dX[k] = J_X[k] * dL_du0 + J_X[3 + k] * dL_dv0;
+            /* dL/dx = R^T dL/dX */
+            for (int k = 0; k < 3; ++k)
+                dxyz[i * 3 + k] = (double)T->R[0 * 3 + k] * dX[0] + (double)T->R[1 * 3 + k] * dX[1] +
+                                  (double)T->R[2 * 3 + k] * dX[2];
+            /* Left increment exp(xi)(R,t): X' = X + nu + omega x X, so
+             * dL/dnu = dL/dX and dL/domega = X x dL/dX. */
+            double dxi[6] = {dX[0], dX[1], dX[2],
+                             X[1] * dX[2] - X[2] * dX[1],
+                             X[2] * dX[0] - X[0] * dX[2],
+                             X[0] * dX[1] - X[1] * dX[0]};
+            for (int k = 0; k < 6; ++k) {
+                acc[k] += dxi[k];
+                double dk = J_K[k] * dL_du0 + J_K[6 + k] * dL_dv0;
+                acc[6 + k] += dk;
+            }
+            /* error scale: sum of the magnitudes of each layer's own term */
+            for (int l = 0; l < levels; ++l) {
+                if (tu[l] == 0.0 && tv[l] == 0.0) continue;
+                double eX[3];
+                for (int k = 0; k < 3; ++k) eX[k] = J_X[k] * tu[l] + J_X[3 + k] * tv[l];
+                double exi[6] = {eX[0], eX[1], eX[2],
+                                 X[1] * eX[2] - X[2] * eX[1],
+                                 X[2] * eX[0] - X[0] * eX[2],
+                                 X[0] * eX[1] - X[1] * eX[0]};
+                for (int k = 0; k < 6; ++k) {
+                    acc[12 + k] += fabs(exi[k]);
+                    acc[18 + k] += fabs(J_K[k] * tu[l] + J_K[6 + k] * tv[l]);
+                }
+            }
+        }
+        free(D);
+    }
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 6; ++k) {
+            dpose[k] += part[24 * t + k];
+            dintr[k] += part[24 * t + 6 + k];
+            dpose_abs[k] += part[24 * t + 12 + k];
+            dintr_abs[k] += part[24 * t + 18 + k];
+        }
+    free(part);
     if (log_desc) /* d exp(tau) / d tau = exp(tau) */
         for (int64_t j = 0; j < n * c; ++j) dfeat[j] *= lin[j];
     free(lin);
-    free(D);
-    return 0;
+    return failed ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------ */
