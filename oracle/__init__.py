@@ -331,7 +331,7 @@ class Backward:
 
 
 def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_projected=False,
-             log_desc=False, threads=1, sample=None) -> Backward:
+             log_desc=False, threads=1, sample=None, layer_grads=True) -> Backward:
     """Sec. 3.1's backward pass for one camera; G is dL/dI over the
     concatenated pyramid (same layout as ``fwd.img``).  sample: point indices
     to visit (None = all): only their rows are written and only their terms
@@ -346,8 +346,9 @@ def backward(fwd: Forward, xyz, feat, cam, G, alpha=0.01, background=None, all_p
     dfeat = np.empty((n, c))
     dxyz = np.empty((n, 3))
     dpose, dintr, dpa, dia = (np.empty(6) for _ in range(4))
-    gu = np.empty((n, fwd.levels))
-    gv = np.empty((n, fwd.levels))
+    # the per-layer g_u, g_v (n x levels each) only when asked for: at 10^8 points they are GBs
+    gu = np.empty((n, fwd.levels)) if layer_grads else None
+    gv = np.empty((n, fwd.levels)) if layer_grads else None
     bg = None if background is None else np.ascontiguousarray(background, dtype=np.float64)
     smp = None if sample is None else np.ascontiguousarray(sample, dtype=np.int64)
     if smp is not None and smp.size and (smp.min() < 0 or smp.max() >= n):

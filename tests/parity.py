@@ -128,9 +128,11 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
 
 def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, grads=None,
                normals=False, epilogue=False, all_projected=False, backward=True, discard=None, leaky=False,
-               log_desc=False, env=None):
+               log_desc=False, env=None, threads=0):
     """The oracle on the same inputs: per camera forward (+ backward), summed
-    over cameras for the per-point gradients."""
+    over cameras for the per-point gradients.  On every core by default: the
+    oracle's results do not depend on its thread count (its pose and
+    intrinsics sums only in FP64 rounding, far below every tolerance here)."""
     feat = scene.feat_as(dtype)
     res = {"keys": [], "cnt": [], "img": [], "dpose": [], "dintr": [], "dpose_abs": [], "dintr_abs": []}
     dfeat = np.zeros((scene.n, scene.c))
@@ -141,7 +143,7 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
         kw["log_desc"] = log_desc
         kw["env"] = None if env is None else np.asarray(env, np.float64)
         f = orc.forward(scene.xyz, feat, cam, levels, alpha, znear, background,
-                        scene.normals if normals else None, **kw)
+                        scene.normals if normals else None, threads=threads, **kw)
         res["keys"].append(f.keys)
         res["cnt"].append(f.cnt)
         img = f.img.copy()
@@ -158,7 +160,8 @@ def oracle_run(orc, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, 
         if backward and G is not None:
             if env is not None:
                 denv += orc.env_grad(f, cam, G, denv.shape)
-            b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected, log_desc)
+            b = orc.backward(f, scene.xyz, feat, cam, G, alpha, background, all_projected, log_desc,
+                             threads=threads, layer_grads=False)
             dfeat += b.dfeat
             dxyz += b.dxyz
             for key in ("dpose", "dintr", "dpose_abs", "dintr_abs"):

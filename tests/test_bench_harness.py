@@ -51,15 +51,26 @@ def test_two_gloo_ranks_max_time():
 
 
 def test_algorithmic_bytes_model():
+    """The measurement plan's per-unit bytes: per point (forward 24 + c s,
+    backward 24 + c s + 4 c, + 12 with a re-run depth pass) and per pyramid
+    pixel; the per-kernel split adds up to the step."""
     import bench
     n, px, c = 1000, 500, 8
-    assert bench.algorithmic_bytes("depth", n, px, c, 2, 2) == n * 12 + px * 16
-    # the backward point pass reads and writes only the points in some Lambda
-    assert bench.algorithmic_bytes("bwd_points", n, px, c, 2, 2, 400) == \
+    # the plan's totals for C = 8: BF16 112 B and FP32 144 B per point
+    assert sum(bench.s8d_point_bytes(8, 2)) == 112 and sum(bench.s8d_point_bytes(8, 4)) == 144
+    assert bench.s8d_point_bytes(8, 2, recompute=True)[1] == 72 + 12
+    assert bench.s8d_pixel_bytes(8, 2) == (8 + 4 + 32 + 4 + 32 + 16, 32)
+    step = bench.s8d_step_bytes(n, px, c, 2, 2)
+    assert step == n * 112 + px * (96 + 32)
+    kernels = ("clear", "depth", "accumulate", "normalize", "bwd_prepass", "bwd_bin", "bwd_points", "bwd_reduce")
+    assert sum(bench.s8d_kernel_bytes(k, n, px, c, 2, 2) for k in kernels) == step
+    assert bench.s8d_kernel_bytes("bwd_prepass", n, px, c, 2, 2) == 0
+    # the implementation's own traffic: the backward point pass reads and
+    # writes only the points in some Lambda, plus its pixel records
+    assert bench.implementation_bytes("depth", n, px, c, 2, 2) == n * 12 + px * 16
+    assert bench.implementation_bytes("bwd_points", n, px, c, 2, 2, 400) == \
         400 * (4 + 4 + 12 + 16 + 32 + 12) + px * 48 + n * 4 + 600 * (32 + 12)
-    assert bench.algorithmic_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
-    with pytest.raises(KeyError):
-        bench.algorithmic_bytes("nope", n, px, c, 2, 2)
+    assert bench.implementation_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
 
 
 def test_clock_summary_merges_nvidia_smi_and_nvml():

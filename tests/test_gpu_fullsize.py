@@ -12,6 +12,10 @@ benchmark times.
   1920x1080 and a 3840x2160 view bit-exact against the oracle's
   descriptor-free forward, and the image at sampled pixels against the mean
   of the descriptors of the points the oracle puts in Lambda there.
+* Large scene forward + backward (120M points, C = 4 BF16, one 1920x1080
+  view, the benchmark's step): the whole forward and backward against the
+  all-core FP64 oracle -- keys and counts bit-exact, the image, dL/dtau and
+  dL/dx of every point, pose and intrinsics.
 """
 import numpy as np
 import pytest
@@ -131,3 +135,22 @@ def test_large_scene_forward(adop, orc, large_scene, res):
         got = imgs[l].reshape(sc.c, -1)[:, sample].T
         assert rel_err(got, ref) <= RTOL_FEAT_F32, (l, rel_err(got, ref))
         off += wl * hl
+
+
+def test_large_scene_forward_backward(adop, orc, large_scene):
+    """120M points, one 1080p view, forward + backward in the benchmark's
+    configuration (kept state, layer masks, binned backward, gradients
+    assigned), against the oracle on every host core: nothing sampled."""
+    sc = large_scene
+    cam = scenes.path_cameras(60, 1920, 1080, seed=1004)[0]
+    G = [scenes.upstream_grad(cam.w, cam.h, LEVELS, sc.c, 4040)]
+    g = gpu_run(adop, sc, [cam], "bf16", grads=G, out_dtype="f32", grad_assign=True)
+    g.pop("frames")
+    import torch
+    torch.cuda.empty_cache()
+    r = oracle_run(orc, sc, [cam], "bf16", grads=G, threads=0)
+    errs = compare(g, r, "bf16", out_dtype="f32")
+    # a real fwd+bwd workload: a million-pixel view, millions of points with gradients
+    assert np.count_nonzero(g["cnt"][0]) > 1_000_000
+    assert np.count_nonzero(np.any(r["dfeat"] != 0, axis=1)) > 1_000_000
+    assert errs["dxyz"] <= RTOL_GRAD
