@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="time the step launched eagerly, not as a CUDA graph")
     ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     return ap.parse_args()
 
 
@@ -409,21 +409,26 @@ def implementation_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_ou
 
 
 def kernel_roofline(ks: dict, n: int, px: int, c: int, s_feat: int, s_out: int, n_vis: int, peak: float,
-                    peak_kind: str, kernel: str | None = None) -> dict:
+                    peak_kind: str, kernel: str | None = None, recorded: bool = True) -> dict:
     """Roofline of one kernel (default: the one with the most device time):
     its algorithmic bytes per launch over its average CUDA-event launch time,
-    against the measured HBM copy bandwidth."""
+    against the measured HBM copy bandwidth; beside it the same for the bytes
+    this implementation moves (implementation_bytes).  `traffic` is the ncu
+    DRAM record of the headline workload, so other workloads pass
+    recorded=False."""
     dom = kernel or max(ks, key=lambda k: ks[k][1])
     launches, dom_ms = ks[dom]
     ab = s8d_kernel_bytes(dom, n, px, c, s_feat, s_out)
+    ib = implementation_bytes(dom, n, px, c, s_feat, s_out, n_vis)
     t = dom_ms / launches * 1e-3
     achieved = ab / t / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "traffic": recorded_traffic(dom),
+            "traffic": recorded_traffic(dom) if recorded else None,
             "algorithmic_bytes_per_launch": ab,
-            "implementation_bytes_per_launch": implementation_bytes(dom, n, px, c, s_feat, s_out, n_vis),
+            "implementation_bytes_per_launch": ib,
+            "frac_implementation_bytes": round(ib / t / 1e9 / peak, 4),
             "avg_launch_ms": round(dom_ms / launches, 4)}
 
 
@@ -853,7 +858,10 @@ def bench_large_fwd_bwd(device, sc, steps: int, warmup: int, flush) -> dict:
                    "value": round(wl.n / (ms * 1e-3), 1), "unit": UNIT,
                    "points_in_lambda": n_vis, "step_bytes_algorithmic": sb,
                    "step_hbm_fraction": round(sb / (ms * 1e-3) / 1e9 / peak, 4),
-                   "roofline": kernel_roofline(ks, wl.n, wl.px, wl.c, wl.s_feat, wl.s_feat, n_vis, peak, peak_kind),
+                   "roofline": kernel_roofline(ks, wl.n, wl.px, wl.c, wl.s_feat, wl.s_feat, n_vis, peak, peak_kind,
+                                               recorded=False),
+                   "step_bytes_implementation": sum(implementation_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, wl.s_feat,
+                                                                         n_vis) * ks[k][0] for k in ks) // steps,
                    "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
         del wl, step
         torch.cuda.empty_cache()
@@ -915,19 +923,33 @@ def bench_large_scene(device, sc, frames: int = 60) -> dict:
     return {"workload": f"{n} points FP32 xyz + C=4 FP16, 60-frame path, forward only, 4 layers", **res}
 
 
-def bench_serving(device, seconds: float = 10.0, rate: float = 200.0) -> dict:
-    """Three resident clouds (1M, 10M, 50M points, C=8); Poisson arrivals at
-    `rate` req/s of random orbit views at 640x480 / 1280x720 / 1920x1080 /
-    3840x2160 (uniform), forward + photometric epilogue.  (i) continuous
-    batching, BF16 descriptors and output; (ii) one request at a time, FP32."""
-    import threading
+def bench_serving(device, seconds: float = 4.0, rates=(200.0, 1000.0, 2000.0), outstanding: int = 64) -> dict:
+    """Three resident clouds (1M, 10M, 50M points, C=8); requests of random
+    orbit views at 640x480 / 1280x720 / 1920x1080 / 3840x2160 (uniform) over
+    a uniformly drawn cloud, forward + photometric epilogue.  Two servers:
+    (i) continuous batching, BF16 descriptors and output (64 slots, 4
+    streams, up to 8 cameras of any clouds per launch); (ii) one request at a
+    time, FP32.  Each is measured under Poisson arrivals at each rate and in
+    a closed loop that keeps `outstanding` requests in flight (the saturated
+    throughput), for `seconds` after a 1 s warm-up.  Latency = submit to
+    device completion.  Output buffers come from a ring of 16 per
+    resolution; a request whose buffer is still in use waits for it (the
+    time the client spent blocked is reported: at rates beyond a server's
+    capacity the queue would otherwise grow without bound)."""
     import torch
     import paper_2110_06635_gb300 as adop
     import scenes
     res_set = ((640, 480), (1280, 720), (1920, 1080), (3840, 2160))
+    ring = 16
     base = [scenes.surfaces_scene(n, 8, seed=1005 + k, size_scale=scenes.SIZE_SCALE_SINGLE_VIEW)
             for k, n in enumerate((1_000_000, 10_000_000, 50_000_000))]
     lut = torch.from_numpy(scenes.crf_gamma_lut()).to(device)
+    rng0 = np.random.default_rng(2026)
+    pool = []  # a fixed pool of requests, cycled
+    for _ in range(512):
+        w, h = res_set[int(rng0.integers(4))]
+        cam = scenes.orbit_cameras(1, seed=int(rng0.integers(1 << 30)), resolutions=((w, h),))[0]
+        pool.append((int(rng0.integers(3)), res_set.index((w, h)), cam))
     out = {}
     for mode in ("bf16_batched", "fp32_unbatched"):
         bf16 = mode.startswith("bf16")
@@ -937,67 +959,78 @@ def bench_serving(device, seconds: float = 10.0, rate: float = 200.0) -> dict:
             f = torch.from_numpy(sc.feat_as("bf16").view(np.int16)).to(device).view(torch.bfloat16) if bf16 \
                 else torch.from_numpy(sc.feat).to(device)
             clouds.append(adop.Points(torch.from_numpy(sc.xyz).to(device), f))
+        bufs = [[torch.empty(adop.output_numel(scenes.Camera(w, h, 1.0, 1.0, 0.0, 0.0), 8, LEVELS), dtype=dt,
+                             device=device) for _ in range(ring)] for (w, h) in res_set]
         srv = adop.Server(mem_budget_bytes=8 << 30, max_slots=64 if bf16 else 1, streams=4 if bf16 else 1,
                           max_batch=8 if bf16 else 1, levels=LEVELS, flags=adop.ADOP_FLAG_EPILOGUE, out_dtype=dt)
         ids = [srv.load_cloud(p) for p in clouds]
-        rng = np.random.default_rng(2026)
-        n_req = int(seconds * rate)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req + int(rate)))
-        reqs = []
-        for k in range(len(arrivals)):
-            w, h = res_set[int(rng.integers(4))]
-            cam = scenes.orbit_cameras(1, seed=int(rng.integers(1 << 30)), resolutions=((w, h),))[0]
-            reqs.append((int(rng.integers(3)), cam))
-        tickets, lock = [], threading.Lock()
-        pending = [0]
-        done_evt = threading.Event()
+        owner = [[None] * ring for _ in res_set]  # ticket last rendered into each buffer
+        nxt = [0] * len(res_set)
+        state = {"k": 0, "blocked": 0.0}
 
-        def reaper():
-            while not done_evt.is_set() or tickets:
-                with lock:
-                    t = tickets.pop(0) if tickets else None
-                if t is None:
-                    time.sleep(0.0005)
-                    continue
-                srv.wait(t, 120_000)
-                with lock:
-                    pending[0] -= 1
+        def submit():
+            cid, ri, cam = pool[state["k"] % len(pool)]
+            state["k"] += 1
+            j = nxt[ri] % ring
+            nxt[ri] += 1
+            if owner[ri][j] is not None:
+                t0 = time.perf_counter()
+                srv.wait(owner[ri][j], 120_000)
+                state["blocked"] += time.perf_counter() - t0
+            t = srv.submit(ids[cid], cam, bufs[ri][j], lut)
+            owner[ri][j] = t
+            return t
 
-        th = threading.Thread(target=reaper, daemon=True)
-        th.start()
-        warm = int(rate)  # the first second warms up and is not measured
-        t0 = time.perf_counter()
-        for k, ((cid, cam), ta) in enumerate(zip(reqs, arrivals)):
-            if k == warm:
-                # drain the warm-up, then measure from here
-                while True:
-                    with lock:
-                        if pending[0] == 0:
-                            break
-                    time.sleep(0.001)
-                srv.reset_stats()
-                t0 = time.perf_counter() - ta
-            delay = t0 + ta - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            buf = torch.empty(adop.output_numel(cam, 8, LEVELS), dtype=dt, device=device)
-            t = srv.submit(ids[cid], cam, buf, lut)
-            with lock:
-                tickets.append(t)
-                pending[0] += 1
-        done_evt.set()
-        th.join()
-        st = srv.stats()
-        out[mode] = {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                     "mean_ms": round(st["mean_ms"], 3), "max_ms": round(st["max_ms"], 3),
-                     "req_per_s": round(st["req_per_s"], 1), "points_per_s": round(st["points_per_s"], 1),
-                     "completed": st["completed"], "mean_batch": round(st["mean_batch"], 2),
-                     "mem_peak_bytes": st["mem_peak"]}
+        def drain():
+            for row in owner:
+                for t in row:
+                    if t is not None:
+                        srv.wait(t, 120_000)
+
+        res = {}
+        for rate in list(rates) + ["saturated"]:
+            rng = np.random.default_rng(7)
+            for phase in ("warm", "measure"):
+                dur = 1.0 if phase == "warm" else seconds
+                state["blocked"] = 0.0
+                t0 = time.perf_counter()
+                if rate == "saturated":
+                    inflight = []
+                    while time.perf_counter() - t0 < dur:
+                        while len(inflight) >= outstanding:
+                            srv.wait(inflight.pop(0), 120_000)
+                        inflight.append(submit())
+                else:
+                    ta = t0
+                    while ta - t0 < dur:
+                        ta += rng.exponential(1.0 / rate)
+                        d = ta - time.perf_counter()
+                        if d > 0:
+                            time.sleep(d)
+                        submit()
+                drain()
+                if phase == "warm":
+                    srv.reset_stats()
+            st = srv.stats()
+            key = "saturated" if rate == "saturated" else f"poisson_{int(rate)}"
+            res[key] = {"offered_req_per_s": None if rate == "saturated" else rate,
+                        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                        "mean_ms": round(st["mean_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                        "req_per_s": round(st["req_per_s"], 1), "points_per_s": round(st["points_per_s"], 1),
+                        "completed": st["completed"], "mean_batch": round(st["mean_batch"], 2),
+                        "mixed_cloud_batches": st["mixed_batches"],
+                        "client_blocked_s": round(state["blocked"], 3)}
+            if rate == "saturated":
+                res[key]["outstanding"] = outstanding
+        res["mem_peak_bytes"] = srv.stats()["mem_peak"]
+        out[mode] = res
         srv.close()
-        del clouds
+        del clouds, bufs
         torch.cuda.empty_cache()
-    out["workload"] = (f"clouds of 1M/10M/50M points (C=8), Poisson {rate:.0f} req/s for {seconds:.0f} s after 1 s "
-                       "warm-up, views at 640x480/1280x720/1920x1080/3840x2160, forward + photometric epilogue")
+    out["workload"] = (f"clouds of 1M/10M/50M points (C=8), views at 640x480/1280x720/1920x1080/3840x2160 "
+                       f"(uniform), forward + photometric epilogue; Poisson arrivals at {', '.join(str(int(r)) for r in rates)} "
+                       f"req/s and a closed loop of {outstanding} outstanding requests, {seconds:.0f} s each after "
+                       "1 s of warm-up")
     return out
 
 

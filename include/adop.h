@@ -33,7 +33,7 @@ extern "C" {
 
 #define ADOP_MAX_LEVELS 8          /* pyramid layers per camera (the paper uses 4) */
 #define ADOP_MAX_CAMERAS 64        /* cameras per call */
-#define ADOP_ABI_VERSION 2
+#define ADOP_ABI_VERSION 3
 
 struct CUstream_st;
 typedef struct CUstream_st* adop_stream; /* == cudaStream_t */
@@ -304,9 +304,12 @@ adop_status adop_pose_apply_tangent(const double* xi, adop_pose* poses, int32_t 
  * create, from which every admitted request reserves its pixel state
  * (keys, counts, sums: (12 + 4 c) bytes per pyramid pixel).  A scheduler
  * thread admits queued requests in FIFO order whenever a slot and memory are
- * free, groups admitted requests of the same cloud (up to max_batch) into
- * one launch sequence, and runs batches concurrently on `streams` CUDA
- * streams; requests that arrive while others run join the next batch.  The
+ * free, groups the oldest admitted requests (up to max_batch, of any of the
+ * resident clouds: each camera of a launch renders its own cloud) into one
+ * launch sequence, and runs batches concurrently on `streams` CUDA streams;
+ * requests that arrive while others run join the next batch.  With
+ * batch_window_us > 0, a batch smaller than max_batch is held back while its
+ * oldest request has waited less than that long, so that more can join.  The
  * render itself is adop_render_forward's (forward pass of Sec. 3.1 plus the
  * photometric epilogue of Sec. 3.3 when ADOP_FLAG_EPILOGUE is set and the
  * camera enables it), so a result is the same alone and in a batch.
@@ -327,6 +330,7 @@ typedef struct {
     const float* background;   /* c FP32 (device) or NULL */
     const float* env;          /* environment map as in adop_params, or NULL */
     int32_t env_w, env_h;
+    int32_t batch_window_us;   /* dynamic batching window, 0 .. 10^6 microseconds (0: launch at once) */
 } adop_serve_config;
 
 typedef struct {
@@ -335,6 +339,7 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms, max_ms;  /* latency since the last reset */
     double req_per_s, points_per_s;          /* completed since the last reset */
     size_t mem_in_use, mem_peak;
+    int64_t mixed_batches;     /* batches whose cameras render more than one cloud */
 } adop_serve_stats;
 
 /* Create a server (allocates the budget and the streams, starts the scheduler). */

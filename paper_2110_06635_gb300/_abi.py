@@ -450,7 +450,8 @@ class adop_serve_config(ct.Structure):
     _fields_ = [("mem_budget_bytes", ct.c_size_t), ("max_slots", ct.c_int32), ("streams", ct.c_int32),
                 ("max_batch", ct.c_int32), ("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float),
                 ("flags", ct.c_uint32), ("out_dtype", ct.c_int32), ("background", ct.c_void_p),
-                ("env", ct.c_void_p), ("env_w", ct.c_int32), ("env_h", ct.c_int32)]
+                ("env", ct.c_void_p), ("env_w", ct.c_int32), ("env_h", ct.c_int32),
+                ("batch_window_us", ct.c_int32)]
 
 
 class adop_serve_stats(ct.Structure):
@@ -458,7 +459,7 @@ class adop_serve_stats(ct.Structure):
                                           "batches")] + \
                [(k, ct.c_double) for k in ("mean_batch", "p50_ms", "p99_ms", "mean_ms", "max_ms", "req_per_s",
                                            "points_per_s")] + \
-               [("mem_in_use", ct.c_size_t), ("mem_peak", ct.c_size_t)]
+               [("mem_in_use", ct.c_size_t), ("mem_peak", ct.c_size_t), ("mixed_batches", ct.c_int64)]
 
 
 SIGNATURES.update({
@@ -491,7 +492,7 @@ class Server:
 
     def __init__(self, mem_budget_bytes: int, max_slots: int = 64, streams: int = 4, max_batch: int = 8,
                  levels: int = 4, alpha: float = 0.01, znear: float = 1e-3, flags: int = 0, out_dtype=None,
-                 background=None, env=None):
+                 background=None, env=None, batch_window_us: int = 0):
         torch = _torch()
         self.lib = load()
         self.levels = levels
@@ -502,7 +503,8 @@ class Server:
         self._env = env
         eh, ew = (0, 0) if env is None else (int(env.shape[0]), int(env.shape[1]))
         cfg = adop_serve_config(mem_budget_bytes, max_slots, streams, max_batch, levels, alpha, znear, flags,
-                                dtype_code(self.out_dtype), _dev_ptr(background), _dev_ptr(env), ew, eh)
+                                dtype_code(self.out_dtype), _dev_ptr(background), _dev_ptr(env), ew, eh,
+                                int(batch_window_us))
         h = ct.c_void_p()
         _check(self.lib.adop_serve_create(ct.byref(cfg), ct.byref(h)))
         self.h = h

@@ -25,6 +25,13 @@ __host__ __device__ constexpr int32_t tiles_along(int32_t n) { return (n + (1 <<
 // Everything a kernel needs to know about one camera, passed by value in the
 // kernel's parameter space (uniform per block: blockIdx.y selects the camera).
 struct DevCam {
+  // the cloud this camera renders in the forward point passes (a launch of
+  // the render entry points gives every camera the same cloud; a server
+  // batch may mix its resident clouds)
+  const float* xyz;
+  const void* feat;
+  const float* normals;  // non-NULL only when normal culling is on
+  int64_t n;
   float R[9];
   float t[3];
   float fx, fy, cx, cy, k1, k2, k3, p1, p2;

@@ -228,6 +228,10 @@ adop_status validate_ws(void* ws, size_t ws_bytes, size_t need) {
 void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_frame_state, const WsLayout& L,
               int k, char* ws, const adop_points* pts, const adop_params* prm) {
   set_camera_constants(d, cam, prm->levels, prm->flags);
+  d.xyz = pts->xyz;
+  d.feat = pts->feat;
+  d.normals = (prm->flags & ADOP_FLAG_NORMAL_CULL) ? pts->normals : nullptr;
+  d.n = pts->n;
   for (int l = 0; l < prm->levels; ++l) {
     if (use_frame_state) {
       d.key[l] = reinterpret_cast<unsigned long long*>(f->key[l]);
@@ -247,7 +251,6 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
     d.bin_off = reinterpret_cast<int32_t*>(ws + L.bin_off[k]);
     d.bin_list = reinterpret_cast<int32_t*>(ws + L.bin_list[k]);
   }
-  (void)pts;
 }
 
 PointArgs point_args(const adop_points* pts, const adop_params* prm, int ncam) {

@@ -100,12 +100,13 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
                                                     const __grid_constant__ PointArgs a) {
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  const float* __restrict__ xyz = cam.xyz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cam.n; i += (int64_t)gridDim.x * blockDim.x) {
     float X0, X1, X2, u0, v0, zd;
-    transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
+    transform(cam, __ldg(xyz + 3 * i), __ldg(xyz + 3 * i + 1), __ldg(xyz + 3 * i + 2), X0, X1, X2);
     if (!camera(cam, X0, X1, X2, u0, v0, zd) || !(zd > a.znear)) continue;
     if (!in_pyramid(u0, v0, cam.w, cam.h, a.levels)) continue;
-    if (a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2)) continue;
+    if (cam.normals && !normal_keep(cam, cam.normals, i, X0, X1, X2)) continue;
     const unsigned long long key = depth_key(zd, i);
     const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
     int32_t pix[kL];  // pixel within layer l (< 2^28), -1: none
@@ -145,13 +146,14 @@ __global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>())
     k_accum(const __grid_constant__ LaunchCams cams, const __grid_constant__ PointArgs a) {
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
-  const TF* feat = reinterpret_cast<const TF*>(a.feat);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  const TF* feat = reinterpret_cast<const TF*>(cam.feat);
+  const float* __restrict__ xyz = cam.xyz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cam.n; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t mask = 0;  // bit l: the point is in Lambda of its layer-l pixel
     float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd;
-    transform(cam, __ldg(a.xyz + 3 * i), __ldg(a.xyz + 3 * i + 1), __ldg(a.xyz + 3 * i + 2), X0, X1, X2);
+    transform(cam, __ldg(xyz + 3 * i), __ldg(xyz + 3 * i + 1), __ldg(xyz + 3 * i + 2), X0, X1, X2);
     if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) && in_pyramid(u0, v0, cam.w, cam.h, a.levels) &&
-        !(a.normals && !normal_keep(cam, a.normals, i, X0, X1, X2))) {
+        !(cam.normals && !normal_keep(cam, cam.normals, i, X0, X1, X2))) {
       const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
       int32_t pix[kL];  // pixel within layer l (< 2^28), -1: none
       uint32_t zb[kL];
@@ -246,20 +248,28 @@ cudaError_t launch_clear(const LaunchCams& cams, const PointArgs& a, int c, cuda
   return e;
 }
 
+int64_t most_points(const LaunchCams& cams, const PointArgs& a) {
+  int64_t most = 0;
+  for (int k = 0; k < a.ncam; ++k) most = cams.c[k].n > most ? cams.c[k].n : most;
+  return most;
+}
+
 cudaError_t launch_depth(const LaunchCams& cams, const PointArgs& a, cudaStream_t s) {
-  if (a.n == 0) return cudaSuccess;
-  if (a.levels <= 4) return launch_strided(k_depth<4>, a.n, a.ncam, kPointWaves, 0, s, cams, a);
-  return launch_strided(k_depth<ADOP_MAX_LEVELS>, a.n, a.ncam, kPointWaves, 0, s, cams, a);
+  const int64_t n = most_points(cams, a);
+  if (n == 0) return cudaSuccess;
+  if (a.levels <= 4) return launch_strided(k_depth<4>, n, a.ncam, kPointWaves, 0, s, cams, a);
+  return launch_strided(k_depth<ADOP_MAX_LEVELS>, n, a.ncam, kPointWaves, 0, s, cams, a);
 }
 
 cudaError_t launch_accum(const LaunchCams& cams, const PointArgs& a, int c, adop_dtype fd, cudaStream_t s) {
-  if (a.n == 0) return cudaSuccess;
+  const int64_t n = most_points(cams, a);
+  if (n == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   if (a.levels <= 4) {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, 4>, a.n, a.ncam, kPointWaves, 0,
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, 4>, n, a.ncam, kPointWaves, 0,
                                                                   s, cams, a)));
   } else {
-    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, ADOP_MAX_LEVELS>, a.n, a.ncam,
+    ADOP_DISPATCH_C(c, ADOP_DISPATCH_T(fd, TF, e = launch_strided(k_accum<kC, TF, ADOP_MAX_LEVELS>, n, a.ncam,
                                                                   kPointWaves, 0, s, cams, a)));
   }
   return e;

@@ -30,7 +30,9 @@ cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
-// Arguments shared by the point kernels of one launch.
+// Arguments shared by the point kernels of one launch.  (The forward depth
+// and accumulate passes read each camera's cloud from its DevCam instead of
+// xyz/feat/normals/n here, so that a server batch can mix clouds.)
 struct PointArgs {
   const float* xyz;
   const void* feat;
@@ -67,6 +69,9 @@ int num_sms();
 int point_blocks(int64_t n, int ncam);
 // Most pyramid pixels of any camera in the launch.
 int64_t most_pixels(const LaunchCams& cams, const PointArgs& a);
+// Most points of any camera's cloud in the launch (the forward point passes
+// take each camera's cloud from its DevCam).
+int64_t most_points(const LaunchCams& cams, const PointArgs& a);
 // Grid of a grid-stride kernel k (kThreads threads, smem bytes of dynamic
 // shared memory) over `work` items per camera: enough blocks for the work, at
 // most `waves` whole waves of the kernel's resident blocks over all SMs,

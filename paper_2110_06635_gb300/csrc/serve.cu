@@ -10,6 +10,7 @@
 // time and notifies; it makes no CUDA call).  Every wait is bounded.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
@@ -107,6 +108,7 @@ struct Server {
   // statistics
   LatencyStats lat;
   int64_t n_submitted = 0, n_completed = 0, n_cancelled = 0, n_failed = 0, n_batches = 0, n_batched_reqs = 0;
+  int64_t n_mixed = 0;  // batches whose cameras render more than one cloud
   double points_done = 0.0;
   Clock::time_point t_start = Clock::now(), t_last{};
   bool any_done = false;
@@ -164,21 +166,29 @@ void Server::launch_locked() {
         break;
       }
     if (s < 0) return;
-    // one batch: the oldest admitted request and up to max_batch - 1 more of the same cloud
-    const int32_t cloud = reqs[admitted.front()].cloud;
-    std::vector<uint64_t> pick;
-    for (size_t k = 0; k < admitted.size() && (int)pick.size() < cfg.max_batch; ++k)
-      if (reqs[admitted[k]].cloud == cloud) pick.push_back(admitted[k]);
-    std::vector<uint64_t> rest;
-    for (uint64_t t : admitted)
-      if (std::find(pick.begin(), pick.end(), t) == pick.end()) rest.push_back(t);
-    admitted.swap(rest);
+    // dynamic batching: a batch smaller than max_batch waits while its oldest
+    // request is younger than the batching window (more requests may join)
+    if ((int)admitted.size() < cfg.max_batch && cfg.batch_window_us > 0) {
+      const double waited_us =
+          std::chrono::duration<double, std::micro>(Clock::now() - reqs[admitted.front()].t_submit).count();
+      if (waited_us < (double)cfg.batch_window_us) return;
+    }
+    // one batch: the oldest admitted requests, up to max_batch, of any cloud
+    // (each camera of a launch renders its own cloud)
+    const size_t take = std::min(admitted.size(), (size_t)cfg.max_batch);
+    std::vector<uint64_t> pick(admitted.begin(), admitted.begin() + take);
+    admitted.erase(admitted.begin(), admitted.begin() + take);
 
     LaunchCams lc;
     for (size_t j = 0; j < pick.size(); ++j) {
       Request& r = reqs[pick[j]];
       DevCam& d = lc.c[j];
       set_camera_constants(d, r.cam, cfg.levels, cfg.flags);
+      const adop_points& P = clouds[r.cloud];
+      d.xyz = P.xyz;
+      d.feat = P.feat;
+      d.normals = (cfg.flags & ADOP_FLAG_NORMAL_CULL) ? P.normals : nullptr;
+      d.n = P.n;
       char* base = pool + r.offset;
       const int64_t px = d.off[cfg.levels];
       const size_t kb = (size_t)px * 8, cb = (size_t)px * 4;
@@ -195,20 +205,16 @@ void Server::launch_locked() {
       }
       r.state = kLaunched;
     }
-    const adop_points& P = clouds[cloud];
-    PointArgs a{};
-    a.xyz = P.xyz;
-    a.feat = P.feat;
-    a.normals = (cfg.flags & ADOP_FLAG_NORMAL_CULL) ? P.normals : nullptr;
+    PointArgs a{};  // (the point passes read each camera's cloud from its DevCam)
     a.background = cfg.background;
     a.env = cfg.env;
     a.env_w = cfg.env_w;
     a.env_h = cfg.env_h;
     a.radius = nullptr;
     a.beta = nullptr;
-    a.n = P.n;
     a.levels = cfg.levels;
     a.ncam = (int32_t)pick.size();
+    a.n = most_points(lc, a);
     a.znear = cfg.znear;
     a.a1 = 1.0f + cfg.alpha;
     a.flags = cfg.flags;
@@ -240,6 +246,11 @@ void Server::launch_locked() {
     stream_busy[s] = true;
     ++n_batches;
     n_batched_reqs += (int64_t)pick.size();
+    for (uint64_t t : pick)
+      if (reqs[t].cloud != reqs[pick.front()].cloud) {
+        ++n_mixed;
+        break;
+      }
     inflight.push_back(std::move(bt));
   }
 }
@@ -266,8 +277,10 @@ void Server::run() {
       launch_locked();
       done_cv.notify_all();
     }
-    // sleep until a submit, a completion or a short poll interval
-    cv.wait_for(lk, std::chrono::microseconds(200));
+    // sleep until a submit, a completion or a short poll interval (which also
+    // ends a batching window)
+    cv.wait_for(lk, std::chrono::microseconds(cfg.batch_window_us > 0 && cfg.batch_window_us < 200
+                                                  ? cfg.batch_window_us : 200));
   }
 }
 
@@ -287,6 +300,8 @@ adop_status adop_serve_create(const adop_serve_config* cfg, adop_server** out) {
   if (cfg->streams < 1 || cfg->streams > 16) return err(ADOP_ERR_INVALID_ARG, "streams outside [1, 16]");
   if (cfg->max_batch < 1 || cfg->max_batch > adop::kMaxCamsPerLaunch)
     return err(ADOP_ERR_INVALID_ARG, "max_batch outside [1, %d]", adop::kMaxCamsPerLaunch);
+  if (cfg->batch_window_us < 0 || cfg->batch_window_us > 1000000)
+    return err(ADOP_ERR_INVALID_ARG, "batch_window_us outside [0, 10^6]");
   if (cfg->levels < 1 || cfg->levels > ADOP_MAX_LEVELS) return err(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
   if (!(cfg->alpha >= 0.0f) || !(cfg->znear >= 0.0f)) return err(ADOP_ERR_INVALID_ARG, "alpha and znear must be >= 0");
   if (cfg->out_dtype != ADOP_F32 && cfg->out_dtype != ADOP_BF16 && cfg->out_dtype != ADOP_F16)
@@ -451,6 +466,7 @@ adop_status adop_serve_get_stats(adop_server* srv, adop_serve_stats* st) {
   st->points_per_s = span > 0 ? s->points_done / span : 0.0;
   st->mem_in_use = s->alloc.in_use();
   st->mem_peak = s->alloc.peak();
+  st->mixed_batches = s->n_mixed;
   return ADOP_OK;
 }
 
@@ -459,7 +475,7 @@ adop_status adop_serve_reset_stats(adop_server* srv) {
   if (!s) return err(ADOP_ERR_INVALID_ARG, "NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat.clear();
-  s->n_completed = s->n_batches = s->n_batched_reqs = 0;
+  s->n_completed = s->n_batches = s->n_batched_reqs = s->n_mixed = 0;
   s->points_done = 0.0;
   s->any_done = false;
   s->t_start = Clock::now();

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
     for name in names:
         assert hasattr(so, name), f"{name} declared in include/ but not exported"
     assert set(names) <= set(adop.SIGNATURES), "binding misses a declared entry point"
-    assert adop.adop_abi_version() == 2
+    assert adop.adop_abi_version() == 3
 
 
 def _structs(adop, n=10, c=4, levels=4, w=64, h=48, flags=0):

@@ -86,6 +86,33 @@ def test_results_alone_equal_results_in_the_mix(adop):
     srv.close()
 
 
+def test_batches_form_and_mix_clouds(adop):
+    """Under a burst, requests are batched (more than one camera per launch,
+    cameras of different clouds in one launch) and every result still equals
+    the render done alone."""
+    import torch
+    clouds = _clouds(torch, adop)
+    flags = adop.ADOP_FLAG_EPILOGUE
+    # a batching window far longer than the burst's submission: batches fill up
+    srv = adop.Server(mem_budget_bytes=512 << 20, max_slots=64, streams=2, max_batch=8, levels=LEVELS,
+                      flags=flags, batch_window_us=50_000)
+    ids = [srv.load_cloud(p) for _, p in clouds]
+    rng = np.random.default_rng(3)
+    cams = [_random_cam(rng, k) for k in range(32)]
+    outs = [torch.empty(adop.output_numel(c, 8, LEVELS), dtype=torch.float32, device="cuda") for c in cams]
+    reqs = [(srv.submit(ids[k % 2], c, o), k % 2, c, o) for k, (c, o) in enumerate(zip(cams, outs))]
+    for t, _, _, _ in reqs:
+        assert srv.wait(t, 60_000) == 0
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["mem_in_use"] == 0
+    assert st["mean_batch"] > 1.0, st
+    assert st["mixed_batches"] >= 1, st
+    for t, cid, cam, out in reqs:
+        ref = _alone(adop, torch, clouds[cid][1], cam, flags)
+        assert_close(out.cpu().numpy(), ref, RTOL_FEAT_F32, f"request {t}")
+    srv.close()
+
+
 def test_admission_timeout_cancel_and_bad_requests(adop):
     import torch
     clouds = _clouds(torch, adop)
