@@ -47,6 +47,8 @@ struct DevCam {
   float* info;   // backward: per pixel {z_min, 1/(1+|Lambda|) (1: empty), <G, I>, 1/|Lambda|}
   float* gpm;    // backward: upstream gradient, pixel-major, g_stride(c) floats per pixel
   uint32_t* vis;  // per point: layer mask (bits 0-7) | layer-0 screen tile << 8 (or NULL)
+  uint8_t* early;  // per point: the layers where it may still pass the fuzzy test, written by the depth
+                   // pass for the accumulate pass (NULL: not kept)
   // screen-tile binning of the visible points for the backward pass
   int32_t tiles_x, tiles;    // kTileShift-pixel tiles per row, total
   int32_t* bin_count;        // per tile: visible points (then the scatter cursor)

@@ -74,11 +74,13 @@ bool finite(float v) { return std::isfinite(v); }
 
 // Workspace: per camera [keys | counts | sums | point layer masks | backward
 // pixel info | pixel-major upstream gradient | tile counts | tile offsets |
-// tile-ordered point list], then the pose/intrinsics block partials.
+// tile-ordered point list | the depth pass's per-point layer bytes], then the
+// pose/intrinsics block partials.
 struct WsLayout {
   size_t key[ADOP_MAX_CAMERAS], cnt[ADOP_MAX_CAMERAS], acc[ADOP_MAX_CAMERAS], vis[ADOP_MAX_CAMERAS];
   size_t info[ADOP_MAX_CAMERAS], gpm[ADOP_MAX_CAMERAS];
   size_t bin_count[ADOP_MAX_CAMERAS], bin_off[ADOP_MAX_CAMERAS], bin_list[ADOP_MAX_CAMERAS];
+  size_t early[ADOP_MAX_CAMERAS];
   bool binning;
   size_t partials;
   size_t total;
@@ -109,6 +111,8 @@ WsLayout layout(const adop_points* pts, const adop_camera* cams, int32_t n_cam, 
     o = align_up(o + (tiles + 1) * 4);
     L.bin_list[k] = o;
     o = align_up(o + (size_t)pts->n * 4);
+    L.early[k] = o;
+    o = align_up(o + (size_t)pts->n);
   }
   L.binning = true;
   L.partials = o;
@@ -244,6 +248,7 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
   }
   d.acc = use_frame_state ? f->acc : reinterpret_cast<float*>(ws + L.acc[k]);
   d.vis = use_frame_state ? f->vis : reinterpret_cast<uint32_t*>(ws + L.vis[k]);
+  d.early = reinterpret_cast<uint8_t*>(ws + L.early[k]);
   d.info = reinterpret_cast<float*>(ws + L.info[k]);
   d.gpm = reinterpret_cast<float*>(ws + L.gpm[k]);
   if (L.binning) {

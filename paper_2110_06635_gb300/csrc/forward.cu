@@ -94,6 +94,14 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
 // the 1080p step).  (Measured on GB300: grouping lanes that share a pixel
 // with __match_any_sync was 4x slower -- the per-group warp intrinsics
 // serialise -- and interleaving two points per thread 25% slower.)
+// The pass also records, per point, the layers where it may still pass the
+// fuzzy test (cam.early, one byte): it cannot where its depth already exceeds
+// f32(z_cur (1 + alpha)) for the key z_cur it read, since keys only decrease
+// (z_cur >= the final z_min, and f32(. * (1 + alpha)) is monotone), so the
+// accumulate pass's test would reject it there as well.  The accumulate
+// pass skips those layers' key reads, and skips outright the points outside
+// the view or behind at every layer (on the 120M-point frame, 70% of the
+// points are outside the view: accumulate 770 -> 581 us).
 // ---------------------------------------------------------------------------
 template <int kL>
 __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ LaunchCams cams,
@@ -103,27 +111,37 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
   const float* __restrict__ xyz = cam.xyz;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cam.n; i += (int64_t)gridDim.x * blockDim.x) {
     float X0, X1, X2, u0, v0, zd;
+    uint32_t em = 0;  // layers where the point may still pass the fuzzy test
     transform(cam, __ldg(xyz + 3 * i), __ldg(xyz + 3 * i + 1), __ldg(xyz + 3 * i + 2), X0, X1, X2);
-    if (!camera(cam, X0, X1, X2, u0, v0, zd) || !(zd > a.znear)) continue;
-    if (!in_pyramid(u0, v0, cam.w, cam.h, a.levels)) continue;
-    if (cam.normals && !normal_keep(cam, cam.normals, i, X0, X1, X2)) continue;
-    const unsigned long long key = depth_key(zd, i);
-    const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
-    int32_t pix[kL];  // pixel within layer l (< 2^28), -1: none
+    if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) && in_pyramid(u0, v0, cam.w, cam.h, a.levels) &&
+        !(cam.normals && !normal_keep(cam, cam.normals, i, X0, X1, X2))) {
+      const unsigned long long key = depth_key(zd, i);
+      const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
+      int32_t pix[kL];  // pixel within layer l (< 2^28), -1: none
 #pragma unroll
-    for (int l = 0; l < kL; ++l) {
-      int32_t pu, pv;
-      const bool keep = l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
-      pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
+      for (int l = 0; l < kL; ++l) {
+        int32_t pu, pv;
+        const bool keep = l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
+        pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
+      }
+      // (an L1-cached read may be stale, but keys only decrease: a stale value
+      // can cost an atomic that loses, never skip one that wins, and it can
+      // only keep a layer in the mask that a fresh value would have dropped)
+      unsigned long long cur[kL];
+#pragma unroll
+      for (int l = 0; l < kL; ++l) cur[l] = pix[l] >= 0 ? __ldca(cam.key[l] + pix[l]) : 0ull;
+#pragma unroll
+      for (int l = 0; l < kL; ++l) {
+        if (pix[l] < 0) continue;
+        if (key < cur[l]) {
+          atomicMin(cam.key[l] + pix[l], key);
+          em |= 1u << l;
+        } else if (!(zd > __fmul_rn(__uint_as_float((uint32_t)(cur[l] >> 32)), a.a1))) {
+          em |= 1u << l;  // behind the current nearest point, but within the fuzzy threshold
+        }
+      }
     }
-    // (an L1-cached read may be stale, but keys only decrease: a stale value
-    // can cost an atomic that loses, never skip one that wins)
-    unsigned long long cur[kL];
-#pragma unroll
-    for (int l = 0; l < kL; ++l) cur[l] = pix[l] >= 0 ? __ldca(cam.key[l] + pix[l]) : 0ull;
-#pragma unroll
-    for (int l = 0; l < kL; ++l)
-      if (pix[l] >= 0 && key < cur[l]) atomicMin(cam.key[l] + pix[l], key);
+    if (cam.early) __stcs(cam.early + i, (uint8_t)em);
   }
 }
 
@@ -150,8 +168,16 @@ __global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>())
   const float* __restrict__ xyz = cam.xyz;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cam.n; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t mask = 0;  // bit l: the point is in Lambda of its layer-l pixel
+    // the depth pass's mask and the position are loaded together (no added
+    // round trip); a point that can pass at no layer costs nothing more
+    const uint32_t em = cam.early ? (uint32_t)__ldcs(cam.early + i) : 0xFFu;
+    const float x0 = __ldg(xyz + 3 * i), x1 = __ldg(xyz + 3 * i + 1), x2 = __ldg(xyz + 3 * i + 2);
+    if (em == 0u) {
+      if (cam.vis) cam.vis[i] = 0u;
+      continue;
+    }
     float X0, X1, X2, u0 = 0.0f, v0 = 0.0f, zd;
-    transform(cam, __ldg(xyz + 3 * i), __ldg(xyz + 3 * i + 1), __ldg(xyz + 3 * i + 2), X0, X1, X2);
+    transform(cam, x0, x1, x2, X0, X1, X2);
     if (camera(cam, X0, X1, X2, u0, v0, zd) && (zd > a.znear) && in_pyramid(u0, v0, cam.w, cam.h, a.levels) &&
         !(cam.normals && !normal_keep(cam, cam.normals, i, X0, X1, X2))) {
       const float rw = a.radius ? __ldg(a.radius + i) : 0.0f, bt = a.radius ? __ldg(a.beta + i) : 0.0f;
@@ -160,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>())
 #pragma unroll
       for (int l = 0; l < kL; ++l) {
         int32_t pu, pv;
-        const bool keep = l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
+        const bool keep = ((em >> l) & 1u) && l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
         pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
       }
 #pragma unroll
