@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 120M-point large scene")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--record-traffic", nargs="+", metavar="NCU_CSV",
+                    help="write profiles/ncu_traffic.json from ncu --csv logs of single-kernel captures "
+                         "(DRAM bytes and L2 atomic requests per launch) and exit")
     return ap.parse_args()
 
 
@@ -302,6 +305,67 @@ def recorded_atomics(kernel: str):
     if h.hexdigest() != d["sources_sha1"]:
         return None
     return d["l2_atomic_requests_per_launch"], d.get("l2_atomic_unit_active_pct")
+
+
+# bench name of each library kernel (the k_bin_* launches are one entry)
+NCU_KERNELS = {"k_clear": "clear", "k_depth": "depth", "k_accum": "accumulate", "k_normalize": "normalize",
+               "k_bwd_prepass": "bwd_prepass", "k_bin_count_blk": "bwd_bin", "k_bin_scan": "bwd_bin",
+               "k_bin_scatter_blk": "bwd_bin", "k_bwd_items": "bwd_points", "k_bwd_reduce": "bwd_reduce"}
+NCU_SOURCES = {"forward": ["paper_2110_06635_gb300/csrc/forward.cu", "paper_2110_06635_gb300/csrc/adop_device.cuh"],
+               "backward": ["paper_2110_06635_gb300/csrc/backward.cu", "paper_2110_06635_gb300/csrc/adop_device.cuh"]}
+
+
+def record_traffic(csv_paths) -> dict:
+    """profiles/ncu_traffic.json from ncu --csv logs (metrics
+    gpu__time_duration.sum, dram__bytes_read.sum, dram__bytes_write.sum,
+    lts__t_requests_op_atom.sum, lts__t_requests_op_red.sum and
+    lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed),
+    each capturing launches of one kernel: per bench kernel name, the mean
+    per launch, with the SHA-1 of the sources it was taken from (bench.py
+    reports a record only while the hash matches)."""
+    import csv
+    import hashlib
+    launches = {}  # (bench name, ncu kernel, launch id) -> {metric: value}
+    for path in csv_paths:
+        with open(path) as f:
+            rows = [r for r in csv.reader(f) if r]
+        head = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+        cols = rows[head]
+        ki, mi, vi, ii = (cols.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "ID"))
+        for r in rows[head + 1:]:
+            if len(r) <= vi:
+                continue
+            base = r[ki].split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
+            name = NCU_KERNELS.get(base)
+            if name is None:
+                continue
+            launches.setdefault((name, r[ki].split("(")[0].replace("void ", "").replace("adop::", "").strip(), r[ii]),
+                                {})[r[mi]] = float(r[vi].replace(",", ""))
+    out = {}
+    for name in sorted(set(k[0] for k in launches)):
+        per_kernel = {}
+        for (nm, kern, _), m in launches.items():
+            if nm == name:
+                per_kernel.setdefault(kern, []).append(m)
+        # a bench entry made of several kernels (binning) sums their per-launch means
+        dram = sum(np.mean([x.get("dram__bytes_read.sum", 0) + x.get("dram__bytes_write.sum", 0) for x in v])
+                   for v in per_kernel.values())
+        atom = sum(np.mean([x.get("lts__t_requests_op_atom.sum", 0) + x.get("lts__t_requests_op_red.sum", 0)
+                            for x in v]) for v in per_kernel.values())
+        dur = sum(np.mean([x.get("gpu__time_duration.sum", 0) for x in v]) for v in per_kernel.values())
+        busy = max(np.mean([x.get("lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed", 0)
+                            for x in v]) for v in per_kernel.values())
+        src = NCU_SOURCES["forward" if name in ("clear", "depth", "accumulate", "normalize") else "backward"]
+        h = hashlib.sha1()
+        for rel in src:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        out[name] = {"kernel": " + ".join(sorted(per_kernel)), "launches_captured": sum(len(v) for v in per_kernel.values()),
+                     "dram_bytes_per_launch": int(round(dram)), "l2_atomic_requests_per_launch": int(round(atom)),
+                     "l2_atomic_unit_active_pct": round(float(busy), 2),
+                     "ncu_duration_us": round(float(dur) / 1e3, 2),  # gpu__time_duration.sum is in ns
+                     "sources": src, "sources_sha1": h.hexdigest()}
+    return out
 
 
 def atomic_peaks(device, px: int, ops: int = 1 << 26) -> dict:
@@ -1057,6 +1121,13 @@ def atomic_roofline(device, wl, ks) -> dict:
 
 def main():
     args = parse()
+    if args.record_traffic:
+        rec = record_traffic(args.record_traffic)
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
+            json.dump(rec, f, indent=1)
+            f.write("\n")
+        print(json.dumps({k: (v["dram_bytes_per_launch"], v["l2_atomic_requests_per_launch"]) for k, v in rec.items()}))
+        return
     if args.impl == "reference":
         return main_reference(args)
     dist, rank, world = dist_setup()
