@@ -461,8 +461,8 @@ def implementation_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_ou
     nv = n if n_vis is None else n_vis
     return {
         "clear": px * (8 + 4 + 4 * c),                          # write key, count, sums
-        "depth": n * 12 + px * 8 * 2,                           # read xyz; read+write keys
-        "accumulate": n * (12 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, tau -> mask; keys; RMW count+sums
+        "depth": n * (12 + 1) + px * 8 * 2,                     # read xyz -> layer byte; read+write keys
+        "accumulate": n * (12 + 1 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, byte, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
         "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
         "bwd_bin": n * 8 + nv * 4,                                    # masks twice -> list

@@ -67,7 +67,7 @@ def test_algorithmic_bytes_model():
     assert bench.s8d_kernel_bytes("bwd_prepass", n, px, c, 2, 2) == 0
     # the implementation's own traffic: the backward point pass reads and
     # writes only the points in some Lambda, plus its pixel records
-    assert bench.implementation_bytes("depth", n, px, c, 2, 2) == n * 12 + px * 16
+    assert bench.implementation_bytes("depth", n, px, c, 2, 2) == n * 13 + px * 16
     assert bench.implementation_bytes("bwd_points", n, px, c, 2, 2, 400) == \
         400 * (4 + 4 + 12 + 16 + 32 + 12) + px * 48 + n * 4 + 600 * (32 + 12)
     assert bench.implementation_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
