@@ -498,7 +498,7 @@ def kernel_roofline(ks: dict, n: int, px: int, c: int, s_feat: int, s_out: int, 
 
 class Workload:
     def __init__(self, n_points: int, feat_dtype: str, device: str, scene=None, cam=None, discard: bool = False,
-                 env: bool = False):
+                 env: bool = False, grad_io: str = "f32"):
         import torch
         import paper_2110_06635_gb300 as adop
         import scenes
@@ -541,8 +541,11 @@ class Workload:
         self.ws = adop.alloc_workspace(self.pts, [cam], self.params, None, device)
         G = scenes.upstream_grad(cam.w, cam.h, LEVELS, self.c, 2024)
         self.G_host = G
-        self.G = [torch.from_numpy(g).to(device) for g in G]
-        self.gfeat = torch.empty((self.n, self.c), dtype=torch.float32, device=device)
+        # gradient storage: FP32, or ("bf16") the upstream gradients and dL/dtau
+        # in BF16 (summed in FP32 on the device, rounded once)
+        self.grad_dt = {"f32": torch.float32, "bf16": torch.bfloat16}[grad_io]
+        self.G = [torch.from_numpy(g).to(device).to(self.grad_dt) for g in G]
+        self.gfeat = torch.empty((self.n, self.c), dtype=self.grad_dt, device=device)
         self.gxyz = torch.empty((self.n, 3), dtype=torch.float32, device=device)
         self.gpose = torch.zeros((1, 6), dtype=torch.float32, device=device)
         self.gintr = torch.zeros((1, 6), dtype=torch.float32, device=device)
@@ -558,6 +561,8 @@ class Workload:
         self._lib = lib
         self._ps = self.pts.struct()
         self._pr = self.params.struct()
+        self._pr.grad_dtype = A.dtype_code(self.grad_dt)
+        self._pr.grad_feat_dtype = A.dtype_code(self.grad_dt)
         self._cams = A._cams_array([self.cam])
         self._fr = (A.adop_frame * 1)(self.frame.struct())
         self._g = (ct.c_void_p * LEVELS)(*[g.data_ptr() for g in self.G])
@@ -742,8 +747,10 @@ def e2e_measure(wl, steps: int, warmup: int, device):
     copy to after the last."""
     import torch
     from paper_2110_06635_gb300.pipeline import HostPipeline, StepIO
-    pipe = HostPipeline(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS, device=device)
-    ios = [StepIO.alloc(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS) for _ in range(2)]
+    pipe = HostPipeline(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS, device=device,
+                        grad_dtype=wl.grad_dt, grad_feat_dtype=wl.grad_dt)
+    ios = [StepIO.alloc(wl.cam, wl.n, wl.c, wl.feat.dtype, wl.out_dtype, LEVELS, grad_dtype=wl.grad_dt,
+                        grad_feat_dtype=wl.grad_dt) for _ in range(2)]
     for io in ios:  # two host input sets, used alternately (each step still moves its own bytes)
         io.xyz.copy_(wl.xyz.cpu())
         io.feat.copy_(wl.feat.cpu())
@@ -765,6 +772,40 @@ def _oracle_step(oracle, sc, feat, cam, Gf, idx, threads):
     xyz, fe = (sc.xyz, feat) if idx is None else (sc.xyz[idx], feat[idx])
     f = oracle.forward(xyz, fe, cam, LEVELS, 0.01, 1e-3, threads=threads)
     oracle.backward(f, xyz, fe, cam, Gf, 0.01, threads=threads)
+
+
+def bench_bf16_io(device, steps: int, warmup: int, flush) -> dict:
+    """The headline step with BF16 upstream gradients and BF16 dL/dtau (what
+    a BF16 training step hands the rasterizer and expects back: the library
+    widens the gradients to FP32, sums dL/dtau in FP32 and rounds it once),
+    timed on the device as a CUDA graph and end to end from host buffers."""
+    import ctypes as ct
+    import torch
+    import paper_2110_06635_gb300 as adop
+    wl = Workload(5_000_000, "bf16", device, grad_io="bf16")
+    sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(warmup):
+        wl.step(sp)
+    adop.adop_profile_enable(True)
+    adop.adop_profile_collect()
+    timed_steps(lambda: wl.step(sp), steps, flush, None, device)
+    ks = adop.adop_profile_collect()
+    adop.adop_profile_enable(False)
+    step = wl.graph_step()
+    for _ in range(2):
+        step()
+    total_ms, _ = timed_steps(step, steps, flush, None, device)
+    ksteps = max(30, steps)
+    e2e_ms, bi, bo = e2e_measure(wl, ksteps, 2, device)
+    out = {"workload": "the headline step with the upstream gradients and dL/dtau stored in BF16",
+           "value": round(wl.n * steps / (total_ms / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(total_ms / steps, 4),
+           "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()},
+           "e2e": {"value": round(wl.n * ksteps / (e2e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": bi,
+                   "d2h_bytes_per_step": bo, "steps": ksteps}}
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(budget_s: float = 10.0):
@@ -1184,6 +1225,10 @@ def main():
         bf = results = wl = None  # free the headline workload before the larger ones
         import torch
         torch.cuda.empty_cache()
+        if not args.no_e2e:
+            fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+            line["bf16_io"] = bench_bf16_io(device, args.steps, args.warmup, lambda: fb.zero_())
+            del fb
         if not args.no_discard:
             fb = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
             line["stochastic_discard"] = bench_discard(device, args.steps, args.warmup, lambda: fb.zero_())

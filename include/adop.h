@@ -152,7 +152,15 @@ typedef struct {
  * r_screen = fx r_world / (z 2^l); evaluated in FP32 as
  * (t * t) * f32(gamma * gamma) > 1 - beta with t = (f32(fx 2^-l) * r_world) / z.
  * A discarded (point, layer) pair takes no part in the depth test, the blend
- * or the gradients of that layer. */
+ * or the gradients of that layer.
+ * grad_dtype: storage type of the upstream gradients grad_image of
+ * adop_render_backward(_noalloc) (ADOP_F32, the zero default, or ADOP_BF16 /
+ * ADOP_F16, read and widened to FP32; adop_env_backward and
+ * adop_photometric_backward take ADOP_F32 only).  grad_feat_dtype: storage
+ * type of their grad_feat: ADOP_F32 (default), or ADOP_BF16 / ADOP_F16 with
+ * ADOP_FLAG_GRAD_ASSIGN and one camera, where each point's dL/dtau is summed
+ * in FP32 and rounded once when stored (rows of c 16-bit values, 16-byte
+ * aligned); otherwise ADOP_ERR_UNSUPPORTED.  The forward pass ignores both. */
 typedef struct {
     int32_t levels;
     float alpha;
@@ -162,6 +170,8 @@ typedef struct {
     float gamma;
     const float* env;
     int32_t env_w, env_h;
+    adop_dtype grad_dtype;
+    adop_dtype grad_feat_dtype;
 } adop_params;
 
 /* Per-camera frame.  image[l]: output, c x h_l x w_l planar in out_dtype
@@ -212,9 +222,10 @@ adop_status adop_render_forward(const adop_points* pts, const adop_camera* cams,
 
 /*
  * Backward pass, Sec. 3.1 (Eqs. partial, induce, gradp, spatialderiv,
- * tangent).  grad_image[k * levels + l]: dL/dI of camera k, layer l (FP32,
- * c x h_l x w_l, NULL = zero).  Outputs (FP32, accumulated with += unless
- * ADOP_FLAG_GRAD_ASSIGN):
+ * tangent).  grad_image[k * levels + l]: dL/dI of camera k, layer l (c x h_l
+ * x w_l values of params->grad_dtype, FP32 by default; NULL = zero).
+ * Outputs (FP32 -- grad_feat in params->grad_feat_dtype --, accumulated with
+ * += unless ADOP_FLAG_GRAD_ASSIGN):
  *   grad_feat n x c   dL/dtau = sum over cameras/layers of G(p)/|Lambda(p)| for
  *                     points in Lambda(p)
  *   grad_xyz  n x 3   dL/dx from the one-pixel approximate spatial gradient

@@ -61,7 +61,7 @@ class adop_points(ct.Structure):
 class adop_params(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("alpha", ct.c_float), ("znear", ct.c_float), ("background", ct.c_void_p),
                 ("flags", ct.c_uint32), ("gamma", ct.c_float), ("env", ct.c_void_p), ("env_w", ct.c_int32),
-                ("env_h", ct.c_int32)]
+                ("env_h", ct.c_int32), ("grad_dtype", ct.c_int32), ("grad_feat_dtype", ct.c_int32)]
 
 
 class adop_frame(ct.Structure):
@@ -348,7 +348,7 @@ def adop_photometric_backward(cams, params: Params, c: int, frames, grad_image0,
     grad_photo (n_cam x 9: ev, wb[3], vig_c[2], vig_a[3]) and grad_crf (the
     LUTs' gradients, camera after camera) from dL/d(layer-0 image)."""
     torch = _torch()
-    g1 = _grad_image_ptrs([[g] for g in grad_image0], cams, 1, c)
+    g1, _ = _grad_image_ptrs([[g] for g in grad_image0], cams, 1, c, fp32_only=True)
     g0 = (ct.c_void_p * len(cams))(*[g1[k] for k in range(len(cams))])
     lib = load()
     pr = params.struct()
@@ -370,7 +370,7 @@ def adop_env_backward(cams, params: Params, c: int, frames, grad_images, grad_en
     """Gradient of the environment map params.env (Sec. 3.1), accumulated into
     grad_env (same shape) from grad_images[k][l] (dL/dI of camera k, layer l)
     at the pixels where no point landed."""
-    gi = _grad_image_ptrs(grad_images, cams, params.levels, c)
+    gi, _ = _grad_image_ptrs(grad_images, cams, params.levels, c, fp32_only=True)
     lib = load()
     pr = params.struct()
     arr = _cams_array(cams, crf_luts)
@@ -379,26 +379,36 @@ def adop_env_backward(cams, params: Params, c: int, frames, grad_images, grad_en
                                  _stream_ptr(stream)))
 
 
-def _grad_image_ptrs(grad_images, cams, levels: int, c: int):
-    """Pointer array grad_image[k * levels + l] of the backward entry points.
-    The kernels read each given gradient as c x h_l x w_l float32 values, so
-    anything else (another dtype, another size) is refused here, before any
-    launch."""
+def _grad_image_ptrs(grad_images, cams, levels: int, c: int, fp32_only: bool = False):
+    """Pointer array grad_image[k * levels + l] of the backward entry points
+    and the gradients' storage type (the adop_dtype code; FP32 if none is
+    given).  The kernels read each given gradient as c x h_l x w_l values of
+    one type -- float32, or bfloat16 / float16 where the call takes them -- so
+    anything else (another dtype, mixed dtypes, another size) is refused
+    here, before any launch."""
     torch = _torch()
     gptr = (ct.c_void_p * (len(cams) * levels))()
+    dt = None
+    allowed = (torch.float32,) if fp32_only else (torch.float32, torch.bfloat16, torch.float16)
+    given = []
     for k, cam in enumerate(cams):
         row = grad_images[k] if grad_images is not None else None
         for l in range(levels):
             g = row[l] if row is not None else None
             if g is None:
                 continue
-            if g.dtype != torch.float32:
-                raise ValueError(f"grad_images[{k}][{l}] must be float32, got {g.dtype}")
+            if g.dtype not in allowed:
+                raise ValueError(f"grad_images[{k}][{l}] must be {' or '.join(str(a) for a in allowed)}, got {g.dtype}")
+            if dt is not None and g.dtype != dt:
+                raise ValueError(f"grad_images mix {dt} and {g.dtype}: one storage type per call")
+            dt = g.dtype
             want = c * (int(cam.h) >> l) * (int(cam.w) >> l)
             if g.numel() != want:
                 raise ValueError(f"grad_images[{k}][{l}] has {g.numel()} elements, c x h_l x w_l = {want} expected")
-            gptr[k * levels + l] = _dev_ptr(g)
-    return gptr
+            given.append((k * levels + l, g))
+    for j, g in given:  # every check passed: marshal
+        gptr[j] = _dev_ptr(g)
+    return gptr, (ADOP_F32 if dt is None else dtype_code(dt))
 
 
 def adop_render_forward(points: Points, cams, params: Params, frames, workspace, stream=None, crf_luts=None):
@@ -415,10 +425,14 @@ def adop_render_backward(points: Points, cams, params: Params, frames, grad_imag
                          grad_xyz=None, grad_pose=None, grad_intr=None, workspace=None, stream=None,
                          crf_luts=None):
     """Backward pass (Sec. 3.1).  grad_images[k][l]: dL/dI of camera k, layer l
-    (float32 CUDA tensor c x h_l x w_l or None)."""
-    gptr = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
+    (CUDA tensor c x h_l x w_l or None; float32, bfloat16 or float16, one type
+    per call).  grad_feat: float32, or bfloat16 / float16 with
+    ADOP_FLAG_GRAD_ASSIGN and one camera (summed in FP32, rounded once)."""
+    gptr, gdt = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
     lib = load()
     ps, pr = points.struct(), params.struct()
+    pr.grad_dtype = gdt
+    pr.grad_feat_dtype = ADOP_F32 if grad_feat is None else dtype_code(grad_feat.dtype)
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
     wp, wn = _ws_ptr(workspace)
@@ -432,9 +446,11 @@ def adop_render_backward_noalloc(points: Points, cams, params: Params, frames, g
     """adop_render_backward without a workspace: the library's static scratch
     array is used instead (for callers that may not allocate device memory).
     Frames must carry the forward's kept state."""
-    gptr = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
+    gptr, gdt = _grad_image_ptrs(grad_images, cams, params.levels, points.feat.shape[1])
     lib = load()
     ps, pr = points.struct(), params.struct()
+    pr.grad_dtype = gdt
+    pr.grad_feat_dtype = ADOP_F32 if grad_feat is None else dtype_code(grad_feat.dtype)
     arr = _cams_array(cams, crf_luts)
     fr = (adop_frame * len(frames))(*[f.struct() for f in frames])
     _check(lib.adop_render_backward_noalloc(ct.byref(ps), arr, len(cams), ct.byref(pr), fr, gptr,

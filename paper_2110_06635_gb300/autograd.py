@@ -82,18 +82,26 @@ class _Rasterize(torch.autograd.Function):
         dev = xyz.device
         levels = ctx.params.levels
         ncam = len(ctx.cams)
+        # the upstream gradients in their own storage type when they share one
+        # the library reads (it widens them to FP32), else as FP32
+        given = [g for g in grad_out[:ncam * levels] if g is not None]
+        keep = bool(given) and all(g.dtype == given[0].dtype for g in given) and \
+            given[0].dtype in (torch.float32, torch.bfloat16, torch.float16)
         gimgs = []
         for k in range(ncam):
             row = []
             for l in range(levels):
                 g = grad_out[k * levels + l]
-                row.append(None if g is None else g.to(torch.float32).contiguous())
+                row.append(None if g is None else (g if keep else g.to(torch.float32)).contiguous())
             gimgs.append(row)
         n, c = feat.shape
         need_xyz = ctx.needs_input_grad[0]
         need_feat = ctx.needs_input_grad[1]
         need_pose = ctx.needs_input_grad[2] or ctx.needs_input_grad[3]
-        gfeat = torch.empty((n, c), dtype=torch.float32, device=dev) if need_feat else None
+        # dL/dtau is summed in FP32; with one camera the library rounds it to the
+        # descriptors' storage type itself, else it is converted afterwards
+        gf_dtype = feat.dtype if ncam == 1 else torch.float32
+        gfeat = torch.empty((n, c), dtype=gf_dtype, device=dev) if need_feat else None
         gxyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if need_xyz else None
         gpose = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
         gintr = torch.zeros((ncam, 6), dtype=torch.float32, device=dev) if need_pose else None
@@ -105,7 +113,8 @@ class _Rasterize(torch.autograd.Function):
         g_env = None
         if ctx.needs_input_grad[4]:
             g_env = torch.zeros_like(ctx.params.env, dtype=torch.float32)
-            A.adop_env_backward(ctx.cams, params, c, ctx.frames, gimgs, g_env, crf_luts=ctx.crf_luts)
+            g32 = [[None if g is None else g.to(torch.float32) for g in row] for row in gimgs]
+            A.adop_env_backward(ctx.cams, params, c, ctx.frames, g32, g_env, crf_luts=ctx.crf_luts)
         g_feat = None if gfeat is None else gfeat.to(feat.dtype)
         g_xi = None if not ctx.needs_input_grad[2] else gpose.to(ctx.xi_dev)
         g_intr = None if not ctx.needs_input_grad[3] else gintr.to(ctx.intr_dev)

@@ -146,6 +146,9 @@ adop_status validate_common(const adop_points* pts, const adop_camera* cams, int
                                ADOP_FLAG_GRAD_ASSIGN | ADOP_FLAG_DISCARD | ADOP_FLAG_LEAKY_CRF |
                                ADOP_FLAG_LOG_DESCRIPTORS))
     return fail(ADOP_ERR_INVALID_ARG, "unknown flag bits 0x%x", prm->flags);
+  for (adop_dtype d : {prm->grad_dtype, prm->grad_feat_dtype})
+    if (d != ADOP_F32 && d != ADOP_BF16 && d != ADOP_F16)
+      return fail(ADOP_ERR_INVALID_ARG, "unknown gradient dtype %d", (int)d);
   if (prm->flags & ADOP_FLAG_DISCARD) {
     if (!(prm->gamma > 0.0f) || !finite(prm->gamma))
       return fail(ADOP_ERR_INVALID_ARG, "ADOP_FLAG_DISCARD needs a finite gamma > 0");
@@ -277,7 +280,17 @@ PointArgs point_args(const adop_points* pts, const adop_params* prm, int ncam) {
   a.znear = prm->znear;
   a.a1 = 1.0f + prm->alpha;
   a.flags = prm->flags;
+  a.grad_dtype = prm->grad_dtype;
   return a;
+}
+
+// The storage type of grad_feat: 16-bit types only where each point's dL/dtau
+// is complete before its one store (assigned, one camera).
+adop_status check_grad_feat_dtype(const adop_params* prm, int32_t n_cam) {
+  if (prm->grad_feat_dtype != ADOP_F32 && (!(prm->flags & ADOP_FLAG_GRAD_ASSIGN) || n_cam != 1))
+    return fail(ADOP_ERR_UNSUPPORTED,
+                "a 16-bit grad_feat needs ADOP_FLAG_GRAD_ASSIGN and one camera (several cameras and += sum in FP32)");
+  return ADOP_OK;
 }
 
 // Forward passes (clear, depth, accumulate[, normalize]) for cameras [k0, k0+nc).
@@ -512,6 +525,7 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
     return fail(ADOP_ERR_INVALID_ARG, "grad_feat must be 16-byte aligned");
   if (pts->n > 0 && grad_xyz && ((uintptr_t)grad_xyz & 3) != 0)
     return fail(ADOP_ERR_INVALID_ARG, "grad_xyz must be 4-byte aligned");
+  if ((st = check_grad_feat_dtype(params, n_cam)) != ADOP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   const bool assign = (params->flags & ADOP_FLAG_GRAD_ASSIGN) != 0;
@@ -570,6 +584,7 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
     b.partials = want_pose ? reinterpret_cast<float*>(ws + L.partials) : nullptr;
     b.mode = mode;
     b.all_projected = (params->flags & ADOP_FLAG_GRAD_ALL_PROJECTED) ? 1 : 0;
+    b.feat_out = params->grad_feat_dtype;
     bool dense = !b.all_projected;
     for (int j = 0; j < nc; ++j) dense = dense && lc.c[j].vis != nullptr;
     if (dense) {
@@ -612,6 +627,7 @@ adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_came
     return fail(ADOP_ERR_INVALID_ARG, "grad_feat must be 16-byte aligned");
   if (pts->n > 0 && grad_xyz && ((uintptr_t)grad_xyz & 3) != 0)
     return fail(ADOP_ERR_INVALID_ARG, "grad_xyz must be 4-byte aligned");
+  if ((st = check_grad_feat_dtype(params, n_cam)) != ADOP_OK) return st;
   char* ws = nullptr;
   if ((st = noalloc_scratch(&ws)) != ADOP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -646,6 +662,7 @@ adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_came
     b.partials = want_pose ? reinterpret_cast<float*>(ws + L.partials) : nullptr;
     b.mode = mode;
     b.all_projected = (params->flags & ADOP_FLAG_GRAD_ALL_PROJECTED) ? 1 : 0;
+    b.feat_out = params->grad_feat_dtype;
     if ((e = launch_bwd_points(lc, a, b, pts->c, pts->feat_dtype, bx, s)) != cudaSuccess)
       return cuda_fail(e, "backward point pass launch");
     if (want_pose && (e = launch_bwd_reduce(b.partials, nc, bx, grad_pose ? grad_pose + 6 * k0 : nullptr,

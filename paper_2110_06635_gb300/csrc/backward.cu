@@ -33,7 +33,7 @@
 
 namespace adop {
 
-template <int C>
+template <int C, typename TG>
 __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant__ LaunchCams cams,
                                                           const __grid_constant__ PointArgs a) {
   pdl_entry();
@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(kThreads) k_bwd_prepass(const __grid_constant_
     const unsigned long long key = cam.key[l][p];
     float I[C], G[GS];
     load_vec<C>(cam.acc + g * C, I);
-    const float* gl = cam.grad[l];
+    const TG* gl = reinterpret_cast<const TG*>(cam.grad[l]);  // stored as TG, widened to FP32
 #pragma unroll
-    for (int k = 0; k < C; ++k) G[k] = gl ? __ldg(gl + k * np + p) : 0.0f;
+    for (int k = 0; k < C; ++k) G[k] = gl ? to_f32<TG>(gl[k * np + p]) : 0.0f;
     if (n == 0 && !a.env) {
 #pragma unroll
       for (int k = 0; k < C; ++k) I[k] = a.background ? __ldg(a.background + k) : 0.0f;
@@ -156,13 +156,44 @@ __device__ __forceinline__ void chain_rule(const DevCam& cam, float X0, float X1
   gx[2] = cam.R[2] * dX0 + cam.R[5] * dX1 + cam.R[8] * dX2;
 }
 
-// Write one point's dL/dtau and dL/dx: overwrite (streaming stores),
-// accumulate (owner computes) or add atomically (several cameras).
+// One dL/dtau row of C values rounded once to the 16-bit type T, with the
+// widest stores the row allows (16-byte aligned rows).
+template <int C, typename T>
+__device__ __forceinline__ void store_row16(float* grad_feat, int64_t i, const float (&gf)[C]) {
+  T* dst = reinterpret_cast<T*>(grad_feat) + i * C;
+  if constexpr (C % 8 == 0) {
+#pragma unroll
+    for (int v = 0; v < C / 8; ++v) {
+      uint4 w;
+      T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) e[k] = from_f32<T>(gf[8 * v + k]);
+      __stcs(reinterpret_cast<uint4*>(dst) + v, w);
+    }
+  } else if constexpr (C % 4 == 0) {
+    uint2 w;
+    T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = from_f32<T>(gf[k]);
+    __stcs(reinterpret_cast<uint2*>(dst), w);
+  } else {
+#pragma unroll
+    for (int k = 0; k < C; ++k) dst[k] = from_f32<T>(gf[k]);
+  }
+}
+
+// Write one point's dL/dtau and dL/dx: overwrite (streaming stores, dL/dtau
+// in FP32 or rounded to b.feat_out), accumulate (owner computes) or add
+// atomically (several cameras).
 template <int C>
 __device__ __forceinline__ void write_point_grads(const BwdArgs& b, int64_t i, const float (&gf)[C],
                                                   const float (&gx)[3], bool touched) {
   if (b.mode == kGradAssign) {
-    if (b.grad_feat) {
+    if (b.grad_feat && b.feat_out == ADOP_BF16) {
+      store_row16<C, __nv_bfloat16>(b.grad_feat, i, gf);
+    } else if (b.grad_feat && b.feat_out == ADOP_F16) {
+      store_row16<C, __half>(b.grad_feat, i, gf);
+    } else if (b.grad_feat) {
       float* dst = b.grad_feat + i * C;
       if constexpr (C % 4 == 0) {
 #pragma unroll
@@ -705,7 +736,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_bwd_reduce(const float* __re
 cudaError_t launch_bwd_prepass(const LaunchCams& cams, const PointArgs& a, int c, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   const int64_t px = most_pixels(cams, a);
-  ADOP_DISPATCH_C(c, e = launch_strided(k_bwd_prepass<kC>, px, a.ncam, kPixelWaves, 0, s, cams, a));
+  ADOP_DISPATCH_C(c, ADOP_DISPATCH_T((adop_dtype)a.grad_dtype, TG,
+                                     e = launch_strided(k_bwd_prepass<kC, TG>, px, a.ncam, kPixelWaves, 0, s, cams,
+                                                        a)));
   return e;
 }
 

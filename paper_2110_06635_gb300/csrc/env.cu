@@ -135,6 +135,8 @@ extern "C" adop_status adop_env_backward(const adop_camera* cams, int32_t n_cam,
   if (n_cam < 1 || n_cam > ADOP_MAX_CAMERAS) return fail(ADOP_ERR_INVALID_ARG, "n_cam outside [1, 64]");
   if (!channels_supported(c)) return fail(ADOP_ERR_UNSUPPORTED, "channel count has no kernels");
   if (params->levels < 1 || params->levels > ADOP_MAX_LEVELS) return fail(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
+  if (params->grad_dtype != ADOP_F32)
+    return fail(ADOP_ERR_UNSUPPORTED, "this call reads FP32 upstream gradients only (params->grad_dtype = ADOP_F32)");
   for (int k = 0; k < n_cam; ++k) {
     const adop_intrinsics& K = cams[k].K;
     if (K.w < 1 || K.h < 1 || K.w > 16384 || K.h > 16384)

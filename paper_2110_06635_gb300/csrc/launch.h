@@ -50,6 +50,7 @@ struct PointArgs {
   float znear;
   float a1;             // f32(1 + alpha)
   uint32_t flags;
+  int32_t grad_dtype;   // adop_dtype of the upstream gradients (DevCam::grad)
 };
 
 // Backward outputs of one launch.
@@ -61,6 +62,7 @@ struct BwdArgs {
   float* partials;      // [ncam][12][blocks_x] pose (6) + intrinsics (6) block sums
   int32_t mode;         // GradMode
   int32_t all_projected;
+  int32_t feat_out;     // adop_dtype of grad_feat (16-bit types only with kGradAssign)
 };
 
 int num_sms();

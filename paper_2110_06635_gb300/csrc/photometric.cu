@@ -147,6 +147,8 @@ adop_status adop_photometric_backward(const adop_camera* cams, int32_t n_cam, co
   if (n_cam < 1 || n_cam > ADOP_MAX_CAMERAS) return fail(ADOP_ERR_INVALID_ARG, "n_cam outside [1, 64]");
   if (!channels_supported(c)) return fail(ADOP_ERR_UNSUPPORTED, "channel count has no kernels");
   if (params->levels < 1 || params->levels > ADOP_MAX_LEVELS) return fail(ADOP_ERR_INVALID_ARG, "levels outside [1, 8]");
+  if (params->grad_dtype != ADOP_F32)
+    return fail(ADOP_ERR_UNSUPPORTED, "this call reads FP32 upstream gradients only (params->grad_dtype = ADOP_F32)");
   if (params->env && !env_size_ok(params->env_w, params->env_h))
     return fail(ADOP_ERR_INVALID_ARG, "env_w / env_h outside [1, 16384]");
   if (workspace_bytes < adop_photometric_workspace_bytes(n_cam) || !workspace || ((uintptr_t)workspace & 255))

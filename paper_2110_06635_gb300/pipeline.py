@@ -26,9 +26,10 @@ from . import _abi as A
 @dataclass
 class StepIO:
     """Pinned host tensors of one step: inputs xyz (n x 3 FP32), feat (n x c),
-    grads (one c x h_l x w_l FP32 tensor per layer); results images (one
-    c x h_l x w_l tensor per layer, the output dtype), grad_feat (n x c FP32),
-    grad_xyz (n x 3 FP32), grad_pose (6), grad_intr (6)."""
+    grads (one c x h_l x w_l tensor per layer, FP32 or a 16-bit type);
+    results images (one c x h_l x w_l tensor per layer, the output dtype),
+    grad_feat (n x c, FP32 or a 16-bit type: summed in FP32 on the device and
+    rounded once), grad_xyz (n x 3 FP32), grad_pose (6), grad_intr (6)."""
     xyz: torch.Tensor
     feat: torch.Tensor
     grads: list
@@ -39,13 +40,14 @@ class StepIO:
     grad_intr: torch.Tensor
 
     @staticmethod
-    def alloc(cam, n: int, c: int, feat_dtype=torch.float32, out_dtype=torch.float32, levels: int = 4):
+    def alloc(cam, n: int, c: int, feat_dtype=torch.float32, out_dtype=torch.float32, levels: int = 4,
+              grad_dtype=torch.float32, grad_feat_dtype=torch.float32):
         pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)  # noqa: E731
         w, h = int(cam.w), int(cam.h)
         return StepIO(pin((n, 3), torch.float32), pin((n, c), feat_dtype),
-                      [pin((c, h >> l, w >> l), torch.float32) for l in range(levels)],
+                      [pin((c, h >> l, w >> l), grad_dtype) for l in range(levels)],
                       [pin((c, h >> l, w >> l), out_dtype) for l in range(levels)],
-                      pin((n, c), torch.float32), pin((n, 3), torch.float32), pin((6,), torch.float32),
+                      pin((n, c), grad_feat_dtype), pin((n, 3), torch.float32), pin((6,), torch.float32),
                       pin((6,), torch.float32))
 
     def inputs(self):
@@ -68,7 +70,8 @@ class HostPipeline:
     and intrinsics gradients are per step."""
 
     def __init__(self, cam, n: int, c: int, feat_dtype=torch.float32, out_dtype=torch.float32, levels: int = 4,
-                 alpha: float = 0.01, znear: float = 1e-3, flags: int = 0, device="cuda", crf_lut=None):
+                 alpha: float = 0.01, znear: float = 1e-3, flags: int = 0, device="cuda", crf_lut=None,
+                 grad_dtype=torch.float32, grad_feat_dtype=torch.float32):
         self.cam, self.n, self.c, self.levels = cam, n, c, levels
         self.device = torch.device(device)
         self.lib = A.load()
@@ -80,10 +83,10 @@ class HostPipeline:
             s = {
                 "xyz": torch.empty((n, 3), dtype=torch.float32, device=self.device),
                 "feat": torch.empty((n, c), dtype=feat_dtype, device=self.device),
-                "grads": [torch.empty((c, h >> l, w >> l), dtype=torch.float32, device=self.device)
+                "grads": [torch.empty((c, h >> l, w >> l), dtype=grad_dtype, device=self.device)
                           for l in range(levels)],
                 "frame": A.Frame.alloc(cam, c, levels, out_dtype, True, self.device, n),
-                "gfeat": torch.empty((n, c), dtype=torch.float32, device=self.device),
+                "gfeat": torch.empty((n, c), dtype=grad_feat_dtype, device=self.device),
                 "gxyz": torch.empty((n, 3), dtype=torch.float32, device=self.device),
                 "gpose": torch.zeros((1, 6), dtype=torch.float32, device=self.device),
                 "gintr": torch.zeros((1, 6), dtype=torch.float32, device=self.device),
@@ -97,6 +100,8 @@ class HostPipeline:
                                     self.luts, self.device)
         self.wp, self.wn = A._ws_ptr(self.ws)
         self.pr = self.params.struct()
+        self.pr.grad_dtype = A.dtype_code(grad_dtype)
+        self.pr.grad_feat_dtype = A.dtype_code(grad_feat_dtype)
         self.cams = A._cams_array([cam], self.luts)
         self.s_in, self.s_comp, self.s_out = (torch.cuda.Stream(self.device) for _ in range(3))
 

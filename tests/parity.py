@@ -76,8 +76,10 @@ def to_np(t):
 
 def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, background=None, flags=0,
             grads=None, out_dtype="f32", keep_state=True, backward=True, normals=False, crf=True,
-            grad_assign=False, init=0.0, vis=True, discard=None, env=None):
-    """Forward (+ backward) through the C ABI; returns numpy results."""
+            grad_assign=False, init=0.0, vis=True, discard=None, env=None, grad_dtype="f32", grad_feat_dtype="f32"):
+    """Forward (+ backward) through the C ABI; returns numpy results.
+    grad_dtype / grad_feat_dtype: storage types of the upstream gradients and
+    of dL/dtau ("f32", "bf16", "f16")."""
     import torch
     dev = "cuda"
     xyz = torch.from_numpy(scene.xyz).to(dev)
@@ -106,14 +108,15 @@ def gpu_run(adop, scene, cams, dtype="f32", levels=4, alpha=0.01, znear=1e-3, ba
     out["img"] = [np.concatenate([to_np(im).ravel() for im in f.images]) for f in frames]
     if backward:
         n, c = scene.n, scene.c
-        gfeat = torch.full((n, c), init, dtype=torch.float32, device=dev)
+        gfeat = torch.full((n, c), init, dtype=torch_dtype(grad_feat_dtype), device=dev)
         gxyz = torch.full((n, 3), init, dtype=torch.float32, device=dev)
         gpose = torch.full((len(cams), 6), init, dtype=torch.float32, device=dev)
         gintr = torch.full((len(cams), 6), init, dtype=torch.float32, device=dev)
-        gimgs = [[torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in gk] for gk in grads]
+        gimgs = [[torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev).to(torch_dtype(grad_dtype))
+                  for g in gk] for gk in grads]
         adop.adop_render_backward(pts, cams, params, frames, gimgs, gfeat, gxyz, gpose, gintr, ws, crf_luts=luts)
         torch.cuda.synchronize()
-        out["dfeat"] = gfeat.cpu().numpy().astype(np.float64) - init
+        out["dfeat"] = gfeat.float().cpu().numpy().astype(np.float64) - init
         out["dxyz"] = gxyz.cpu().numpy().astype(np.float64) - init
         out["dpose"] = gpose.cpu().numpy().astype(np.float64) - init
         out["dintr"] = gintr.cpu().numpy().astype(np.float64) - init

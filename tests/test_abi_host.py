@@ -144,7 +144,8 @@ def test_env_backward_validates(lib):
 @pytest.mark.parametrize("entry", ["adop_render_backward", "adop_render_backward_noalloc"])
 def test_grad_images_checked_before_launch(lib, entry):
     """Both backward wrappers read every upstream gradient as c x h_l x w_l
-    float32 values: another dtype or size is refused on the host (the tensors
+    values of one floating type (float32, bfloat16 or float16): another
+    dtype, mixed dtypes or another size is refused on the host (the tensors
     here are CPU tensors, so nothing could have been launched)."""
     import numpy as np
     import torch
@@ -156,9 +157,35 @@ def test_grad_images_checked_before_launch(lib, entry):
     params = adop.Params(2, 0.01, 1e-3, None, 0)
     fn = getattr(adop, entry)
     extra = [None] * 4 + ([torch.zeros(1)] if entry == "adop_render_backward" else [])
-    bad_dtype = [[torch.zeros((4, 48, 64), dtype=torch.bfloat16), None]]
+    bad_dtype = [[torch.zeros((4, 48, 64), dtype=torch.int32), None]]
     with pytest.raises(ValueError, match="float32"):
         fn(pts, [cam], params, [None], bad_dtype, *extra)
+    mixed = [[torch.zeros((4, 48, 64), dtype=torch.bfloat16), torch.zeros((4, 24, 32))]]
+    with pytest.raises(ValueError, match="mix"):
+        fn(pts, [cam], params, [None], mixed, *extra)
     bad_size = [[None, torch.zeros((4, 24, 31))]]
     with pytest.raises(ValueError, match="elements"):
         fn(pts, [cam], params, [None], bad_size, *extra)
+
+
+def test_gradient_dtype_rules(lib):
+    """The backward's storage types are checked before any launch: a 16-bit
+    grad_feat only when gradients are assigned for one camera; an unknown
+    dtype code is an argument error."""
+    adop, so = lib
+    from paper_2110_06635_gb300 import _abi as A
+    pts, cam, prm, fr = _structs(adop)
+    for k in range(4):
+        fr[0].key[k] = 0x300000
+        fr[0].count[k] = 0x400000
+    fr[0].acc = 0x500000
+    g = (ct.c_void_p * 4)()
+    call = lambda: so.adop_render_backward(ct.byref(pts), cam, 1, ct.byref(prm), fr, g, 0x600000, None, None, None,
+                                           0x100000, 1 << 40, None)
+    prm.grad_feat_dtype = A.ADOP_BF16
+    assert call() == 2 and "ADOP_FLAG_GRAD_ASSIGN" in adop.adop_last_error()
+    prm.grad_feat_dtype = 7
+    assert call() == 1 and "dtype" in adop.adop_last_error()
+    prm.grad_feat_dtype = A.ADOP_F32
+    prm.grad_dtype = 9
+    assert call() == 1 and "dtype" in adop.adop_last_error()

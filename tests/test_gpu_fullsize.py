@@ -9,9 +9,8 @@ benchmark times.
   and backward of that camera), and the one-call backward of all 16 cameras
   against the sum of 16 one-camera calls -- a property that holds at any size.
 * Large scene (120M points, C = 4 FP16, forward): keys and counts of a
-  1920x1080 and a 3840x2160 view bit-exact against the oracle's
-  descriptor-free forward, and the image at sampled pixels against the mean
-  of the descriptors of the points the oracle puts in Lambda there.
+  1920x1080 and a 3840x2160 view bit-exact, and the whole image of every
+  layer, against the all-core FP64 oracle.
 * Large scene forward + backward (120M points, C = 4 BF16, one 1920x1080
   view, the benchmark's step): the whole forward and backward against the
   all-core FP64 oracle -- keys and counts bit-exact, the image, dL/dtau and
@@ -21,8 +20,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import (RTOL_FEAT_F32, RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run,
-                    rel_err)
+from parity import (RTOL_FEAT_F32, RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -93,10 +91,14 @@ def _fp16_tensor(scene):
 
 @pytest.mark.parametrize("res", [(1920, 1080), (3840, 2160)], ids=["1080p", "4k"])
 def test_large_scene_forward(adop, orc, large_scene, res):
+    """120M points, FP16 descriptors, forward only as the benchmark's large-scene
+    leg runs it (no kept state in the frame): keys and counts bit-exact and the
+    whole image of every layer against the all-core FP64 oracle."""
     import torch
     sc = large_scene
     cam = scenes.path_cameras(60, *res, seed=1004)[0]
-    pts = adop.Points(torch.from_numpy(sc.xyz).cuda(), _fp16_tensor(sc))
+    feat16 = np.ascontiguousarray(sc.feat.astype(np.float16))
+    pts = adop.Points(torch.from_numpy(sc.xyz).cuda(), torch.from_numpy(feat16).cuda())
     params = adop.Params(LEVELS, 0.01, 1e-3, None, 0)
     fr = adop.Frame.alloc(cam, sc.c, LEVELS, torch.float32, True, "cuda")
     ws = adop.alloc_workspace(pts, [cam], params, None, "cuda")
@@ -104,37 +106,14 @@ def test_large_scene_forward(adop, orc, large_scene, res):
     torch.cuda.synchronize()
     keys = fr.key.cpu().numpy().view(np.uint64)
     cnt = fr.count.cpu().numpy().view(np.uint32)
-    imgs = [im.cpu().numpy() for im in fr.images]
+    img = np.concatenate([im.cpu().numpy().ravel() for im in fr.images])
     del pts, fr, ws
     torch.cuda.empty_cache()
-    r = orc.keys_counts(sc.xyz, cam, LEVELS)
+    r = orc.forward(sc.xyz, feat16, cam, LEVELS, 0.01, 1e-3, threads=0)
     assert np.array_equal(keys, r.keys), f"{np.count_nonzero(keys != r.keys)} keys differ"
     assert np.array_equal(cnt, r.cnt)
     assert np.count_nonzero(cnt) > 0.5 * cnt.size
-    # sampled pixels of every layer: the mean over the points the oracle puts
-    # in Lambda (z <= f32(z_min * f32(1 + alpha))), in FP64
-    rng = np.random.default_rng(77)
-    a1 = np.float32(1.0) + np.float32(0.01)
-    off = 0
-    for l in range(LEVELS):
-        wl, hl = cam.w >> l, cam.h >> l
-        lk = r.keys[off:off + wl * hl]
-        hit = np.flatnonzero(r.cnt[off:off + wl * hl])
-        sample = np.sort(rng.choice(hit, min(400, hit.size), replace=False))
-        pl = r.pix[:, l]
-        sel = np.flatnonzero(np.isin(pl, sample))
-        zmin = (lk[pl[sel]] >> np.uint64(32)).astype(np.uint32).view(np.float32)
-        inl = sel[r.z[sel] <= zmin * a1]
-        ref = np.zeros((sample.size, sc.c))
-        n = np.zeros(sample.size)
-        idx = np.searchsorted(sample, pl[inl])
-        np.add.at(ref, idx, sc.feat[inl].astype(np.float16).astype(np.float64))
-        np.add.at(n, idx, 1.0)
-        assert np.array_equal(n, r.cnt[off + sample])
-        ref /= n[:, None]
-        got = imgs[l].reshape(sc.c, -1)[:, sample].T
-        assert rel_err(got, ref) <= RTOL_FEAT_F32, (l, rel_err(got, ref))
-        off += wl * hl
+    assert_close(img, r.img, RTOL_FEAT_F32, f"{res} image")
 
 
 def test_large_scene_forward_backward(adop, orc, large_scene):

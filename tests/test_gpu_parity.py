@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import compare, epilogue_decidable_grads, gpu_run, oracle_run
+from parity import RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run, torch_dtype
 
 pytestmark = pytest.mark.gpu
 
@@ -196,3 +196,26 @@ def test_fisheye_camera(adop, orc, dtype):
     r = oracle_run(orc, sc, [cam], dtype, grads=G)
     compare(g, r, dtype)
     assert (g["cnt"][0] > 0).sum() > 1000
+
+
+@pytest.mark.parametrize("gdt", ["bf16", "f16"])
+def test_16bit_gradient_io(adop, orc, gdt):
+    """Upstream gradients stored in BF16 / FP16 and dL/dtau returned in the same
+    type (assigned, one camera).  The gradients are rounded to that type once
+    on the host, so the GPU and the oracle see the same values: dL/dx, pose and
+    intrinsics within the FP32 tolerances, dL/dtau within one 16-bit rounding
+    of the output (RTOL_FEAT_LOWP)."""
+    import torch
+    from parity import RTOL_FEAT_LOWP, assert_reduced
+    sc = scenes.tiny_spheres(20000, 8, seed=71)
+    cams = [scenes.tiny_camera()]
+    G = [[torch.from_numpy(g).to(torch_dtype(gdt)).float().numpy()
+          for g in scenes.upstream_grad(c.w, c.h, 4, sc.c, 72)] for c in cams]
+    g = gpu_run(adop, sc, cams, "bf16", grads=G, grad_assign=True, grad_dtype=gdt, grad_feat_dtype=gdt)
+    r = oracle_run(orc, sc, cams, "bf16", grads=G)
+    assert np.array_equal(g["keys"][0], r["keys"][0]) and np.array_equal(g["cnt"][0], r["cnt"][0])
+    assert_close(g["dfeat"], r["dfeat"], RTOL_FEAT_LOWP, f"dL/dtau stored as {gdt}")
+    assert_close(g["dxyz"], r["dxyz"], RTOL_GRAD, "dL/dx")
+    assert_reduced(g["dpose"][0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
+    assert_reduced(g["dintr"][0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
+    assert np.abs(r["dfeat"]).max() > 0 and np.abs(r["dxyz"]).max() > 0
