@@ -60,13 +60,10 @@ def _effective_cameras(cameras, xi, intrinsics):
 
 class _Rasterize(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, xyz, feat, xi, intr, env, cams, params, out_dtype, keep_state, crf_luts, discard):
-        dev = xyz.device
+    def forward(ctx, xyz, feat, xi, intr, env, cams, params, out_dtype, keep_state, crf_luts, discard, buffers):
         levels = params.levels
         pts = A.Points(xyz.contiguous(), feat.contiguous(), None, *discard)
-        frames = [A.Frame.alloc(c, feat.shape[1], levels, out_dtype, keep_state, dev,
-                                xyz.shape[0] if keep_state else None) for c in cams]
-        ws = A.alloc_workspace(pts, cams, params, crf_luts, dev)
+        frames, ws = buffers  # allocated before the pose was read (see rasterize)
         A.adop_render_forward(pts, cams, params, frames, ws, crf_luts=crf_luts)
         ctx.save_for_backward(xyz, feat)
         ctx.frames, ctx.cams, ctx.params, ctx.ws, ctx.crf_luts = frames, cams, params, ws, crf_luts
@@ -118,7 +115,7 @@ class _Rasterize(torch.autograd.Function):
         g_feat = None if gfeat is None else gfeat.to(feat.dtype)
         g_xi = None if not ctx.needs_input_grad[2] else gpose.to(ctx.xi_dev)
         g_intr = None if not ctx.needs_input_grad[3] else gintr.to(ctx.intr_dev)
-        return gxyz, g_feat, g_xi, g_intr, g_env, None, None, None, None, None, None
+        return gxyz, g_feat, g_xi, g_intr, g_env, None, None, None, None, None, None, None
 
 
 def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01, znear=1e-3, background=None,
@@ -129,13 +126,21 @@ def rasterize(xyz, feat, cameras, xi=None, intrinsics=None, levels=4, alpha=0.01
     radius and beta (float32 per point), stochastic point discarding
     (Eq. discard) with threshold gamma; with env (env_h x env_w x c float32),
     empty pixels sample the environment map."""
-    cams = _effective_cameras(cameras, xi, intrinsics)
     if radius is not None:
         flags |= A.ADOP_FLAG_DISCARD
     if env is not None and env.requires_grad and not keep_state:
         raise ValueError("the environment map's gradient needs keep_state=True (the forward's per-pixel counts)")
     env_data = None if env is None else env.detach().contiguous()
     params = A.Params(levels, alpha, znear, background, flags & ~A.ADOP_FLAG_GRAD_ASSIGN, gamma, env_data)
+    # Frames and workspace depend on the image sizes, not on the pose: they
+    # are allocated first, while the GPU may still run the previous step;
+    # reading a CUDA tangent below waits for it.
+    dev = xyz.device
+    frames = [A.Frame.alloc(c, feat.shape[1], levels, out_dtype, keep_state, dev,
+                            xyz.shape[0] if keep_state else None) for c in cameras]
+    sizing = A.Points(xyz.detach().contiguous(), feat.detach().contiguous(), None, radius, beta)
+    ws = A.alloc_workspace(sizing, cameras, params, crf_luts, dev)
+    cams = _effective_cameras(cameras, xi, intrinsics)
     outs = _Rasterize.apply(xyz, feat, xi, intrinsics, env, cams, params, out_dtype, keep_state, crf_luts,
-                            (radius, beta))
+                            (radius, beta), (frames, ws))
     return [list(outs[k * levels:(k + 1) * levels]) for k in range(len(cameras))]
