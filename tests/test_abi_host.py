@@ -189,3 +189,22 @@ def test_gradient_dtype_rules(lib):
     prm.grad_feat_dtype = A.ADOP_F32
     prm.grad_dtype = 9
     assert call() == 1 and "dtype" in adop.adop_last_error()
+
+
+def test_server_config_refused_before_any_cuda_call(lib):
+    """adop_serve_create checks its configuration on the host and allocates
+    nothing for a bad one: the batching window, batch size, stream and slot
+    counts."""
+    adop, so = lib
+    from paper_2110_06635_gb300 import _abi as A
+    good = dict(mem_budget_bytes=64 << 20, max_slots=8, streams=2, max_batch=4, levels=4, alpha=0.01, znear=1e-3,
+                flags=0, out_dtype=A.ADOP_F32, background=None, env=None, env_w=0, env_h=0, batch_window_us=0)
+    for field, bad, msg in (("batch_window_us", -1, "batch_window_us"), ("batch_window_us", 2_000_000, "batch_window_us"),
+                            ("max_batch", 0, "max_batch"), ("max_batch", 17, "max_batch"), ("streams", 0, "streams"),
+                            ("max_slots", 0, "max_slots"), ("mem_budget_bytes", 1024, "budget"),
+                            ("flags", A.ADOP_FLAG_DISCARD, "flags")):
+        cfg = A.adop_serve_config(**{**good, field: bad})
+        h = ct.c_void_p()
+        assert so.adop_serve_create(ct.byref(cfg), ct.byref(h)) == 1, field
+        assert msg in adop.adop_last_error(), (field, adop.adop_last_error())
+        assert not h.value

@@ -85,3 +85,20 @@ def test_sampled_backward_rows_and_sums(orc):
     assert np.all(np.abs(intr - full.dintr) <= 1e-12 * full.dintr_abs)
     with pytest.raises(IndexError):
         orc.backward(f, sc.xyz, sc.feat, cam, G, 0.01, sample=np.array([sc.n]))
+
+
+def test_forward_options_do_not_depend_on_threads(orc):
+    """The same with every forward option on: an environment map for the
+    empty pixels, stochastic discarding, normal culling and log descriptors."""
+    sc, cam = _mid_scene()
+    rng = np.random.default_rng(8)
+    env = 0.5 + 0.1 * rng.standard_normal((sc.c, 16, 32))
+    radius = np.full(sc.n, 0.02, np.float32)
+    beta = rng.random(sc.n).astype(np.float32)
+    kw = dict(normals=sc.normals, radius=radius, beta=beta, gamma=1.5, log_desc=True, env=env)
+    ref = orc.forward(sc.xyz, 0.1 * sc.feat, cam, 4, 0.01, 1e-3, threads=1, **kw)
+    assert np.count_nonzero(ref.cnt) > 100 and np.count_nonzero(ref.cnt == 0) > 100
+    for t in (3, 0):
+        f = orc.forward(sc.xyz, 0.1 * sc.feat, cam, 4, 0.01, 1e-3, threads=t, **kw)
+        for name in ("keys", "cnt", "img", "pix", "z"):
+            assert np.array_equal(getattr(f, name), getattr(ref, name)), (t, name)
