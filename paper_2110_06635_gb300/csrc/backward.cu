@@ -393,11 +393,8 @@ __device__ __forceinline__ void pair_contrib(const DevCam& cam, const PointArgs&
 #pragma unroll
   for (int c = 0; c < C; ++c) v[c] = G[c] * ip.w;  // ip.w = f32(1/|Lambda|)
   if (spatial_out) {
-    float tau[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) tau[c] = sp[6 + c];
     float g_u, g_v;
-    spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, sp[0], a.a1, tau, g_u, g_v, pol);
+    spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, sp[0], a.a1, sp + 6, g_u, g_v, pol);  // tau read from shared memory
     const float sc = layer_scale(l);
     v[C] = g_u * sc;
     v[C + 1] = g_v * sc;
