@@ -219,3 +219,31 @@ def test_16bit_gradient_io(adop, orc, gdt):
     assert_reduced(g["dpose"][0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
     assert_reduced(g["dintr"][0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
     assert np.abs(r["dfeat"]).max() > 0 and np.abs(r["dxyz"]).max() > 0
+
+
+def test_layer_mask_buffer_only_4_byte_aligned(adop, orc):
+    """The ABI asks only 4-byte alignment of a caller's layer-mask buffer: a
+    buffer 4 bytes past an aligned start (and a point count that is not a
+    multiple of 4) gives the oracle's results."""
+    import torch
+    from parity import assert_reduced
+    sc = scenes.tiny_spheres(20003, 8, seed=75)  # n not a multiple of 4
+    cams = [scenes.tiny_camera()]
+    G = [scenes.upstream_grad(c.w, c.h, 4, sc.c, 76) for c in cams]
+    r = oracle_run(orc, sc, cams, "f32", grads=G)
+    dev = "cuda"
+    pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+    params = adop.Params(4, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+    fr = adop.Frame.alloc(cams[0], sc.c, 4, torch.float32, True, dev, sc.n)
+    fr.vis = torch.empty(sc.n + 1, dtype=torch.int32, device=dev)[1:]  # 4 bytes past an aligned start
+    assert fr.vis.data_ptr() % 16 == 4
+    ws = adop.alloc_workspace(pts, cams, params, None, dev)
+    adop.adop_render_forward(pts, cams, params, [fr], ws)
+    out = [torch.empty((sc.n, sc.c), device=dev), torch.empty((sc.n, 3), device=dev),
+           torch.zeros((1, 6), device=dev), torch.zeros((1, 6), device=dev)]
+    adop.adop_render_backward(pts, cams, params, [fr], [[torch.from_numpy(x).to(dev) for x in G[0]]], *out, ws)
+    assert np.array_equal(fr.key.cpu().numpy().view(np.uint64), r["keys"][0])
+    assert_close(out[0].cpu().numpy(), r["dfeat"], RTOL_GRAD, "dL/dtau")
+    assert_close(out[1].cpu().numpy(), r["dxyz"], RTOL_GRAD, "dL/dx")
+    assert_reduced(out[2].cpu().numpy()[0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
+    assert_reduced(out[3].cpu().numpy()[0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
