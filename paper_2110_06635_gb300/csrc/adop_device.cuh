@@ -51,9 +51,11 @@ struct DevCam {
                    // pass for the accumulate pass (NULL: not kept)
   // screen-tile binning of the visible points for the backward pass
   int32_t tiles_x, tiles;    // kTileShift-pixel tiles per row, total
-  int32_t* bin_count;        // per tile: visible points (then the scatter cursor)
+  int32_t* bin_count;        // per tile: visible points (the scatter cursor of the path without a table)
   int32_t* bin_off;          // tiles + 1 exclusive offsets
   int32_t* bin_list;         // visible point indices, tile by tile (NULL: no binning)
+  int32_t* bin_table;        // [block][tile]: a binning block's first slot within the tile's range
+  int32_t bin_rows;          // binning blocks the table has rows for
   // photometric epilogue (Sec. 3.3); ev_scale = 2^-EV, computed on the host
   int32_t epi;
   int32_t leaky;  // training response curve (Eq. resonseleak) instead of clamping

@@ -80,7 +80,8 @@ struct WsLayout {
   size_t key[ADOP_MAX_CAMERAS], cnt[ADOP_MAX_CAMERAS], acc[ADOP_MAX_CAMERAS], vis[ADOP_MAX_CAMERAS];
   size_t info[ADOP_MAX_CAMERAS], gpm[ADOP_MAX_CAMERAS];
   size_t bin_count[ADOP_MAX_CAMERAS], bin_off[ADOP_MAX_CAMERAS], bin_list[ADOP_MAX_CAMERAS];
-  size_t early[ADOP_MAX_CAMERAS];
+  size_t early[ADOP_MAX_CAMERAS], bin_table[ADOP_MAX_CAMERAS];
+  int32_t bin_rows;
   bool binning;
   size_t partials;
   size_t total;
@@ -113,7 +114,10 @@ WsLayout layout(const adop_points* pts, const adop_camera* cams, int32_t n_cam, 
     o = align_up(o + (size_t)pts->n * 4);
     L.early[k] = o;
     o = align_up(o + (size_t)pts->n);
+    L.bin_table[k] = o;
+    if (tiles <= (size_t)kBinSmemTiles) o = align_up(o + (size_t)bin_table_rows(n_cam) * tiles * 4);
   }
+  L.bin_rows = bin_table_rows(n_cam);
   L.binning = true;
   L.partials = o;
   o = align_up(o + (size_t)n_cam * kMaxPartialBlocks * 12 * 4);
@@ -258,6 +262,8 @@ void fill_cam(DevCam& d, const adop_camera& cam, const adop_frame* f, bool use_f
     d.bin_count = reinterpret_cast<int32_t*>(ws + L.bin_count[k]);
     d.bin_off = reinterpret_cast<int32_t*>(ws + L.bin_off[k]);
     d.bin_list = reinterpret_cast<int32_t*>(ws + L.bin_list[k]);
+    d.bin_table = reinterpret_cast<int32_t*>(ws + L.bin_table[k]);
+    d.bin_rows = L.bin_rows;
   }
 }
 

@@ -10,6 +10,15 @@
 
 namespace adop {
 
+// Screen-tile binning of the backward's visible points: block-local counts in
+// shared memory up to kBinSmemTiles tiles per camera; the count kernel keeps
+// each block's first slot within every tile's range in a [block][tile] table
+// of bin_table_rows(n_cam) rows per camera (kBinTableBlocks blocks over all
+// cameras at most), so that the scatter reads the layer masks only once.
+constexpr int kBinSmemTiles = 8192;
+constexpr int kBinTableBlocks = 1536;
+inline int bin_table_rows(int ncam) { return (kBinTableBlocks + ncam - 1) / ncam; }
+
 // Launches kernel k on stream s as a programmatic dependent of the work before
 // it in the stream.  The kernel must call pdl_entry() before its first memory
 // access (a CPU test checks every kernel launched this way); it then runs in
