@@ -29,6 +29,7 @@ library's host-side adop_pose_apply_tangent, in FP64.
 from __future__ import annotations
 
 import copy
+import dataclasses
 
 import numpy as np
 import torch
@@ -66,7 +67,13 @@ class _Rasterize(torch.autograd.Function):
         frames, ws = buffers  # allocated before the pose was read (see rasterize)
         A.adop_render_forward(pts, cams, params, frames, ws, crf_luts=crf_luts)
         ctx.save_for_backward(xyz, feat)
-        ctx.frames, ctx.cams, ctx.params, ctx.ws, ctx.crf_luts = frames, cams, params, ws, crf_luts
+        # the backward needs the frames' per-pixel state, not their images: the
+        # images are this Function's outputs, and holding them here would make
+        # a reference cycle (output -> grad_fn -> ctx -> output) that keeps
+        # every step's frames and workspace alive until Python's cycle
+        # collector runs
+        ctx.frames = [dataclasses.replace(f, images=[]) for f in frames]
+        ctx.cams, ctx.params, ctx.ws, ctx.crf_luts = cams, params, ws, crf_luts
         ctx.discard = discard
         ctx.has_xi, ctx.has_intr = xi is not None, intr is not None
         ctx.xi_dev = None if xi is None else xi.device
