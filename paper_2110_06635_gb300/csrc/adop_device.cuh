@@ -268,6 +268,18 @@ __device__ __forceinline__ bool pixel_at(float u0, float v0, int l, int32_t w, i
   return pu >= 0 && pu < wl && pv >= 0 && pv < hl;
 }
 
+// pixel_at for a position that passed in_pyramid: there |u0 2^-l| and
+// |v0 2^-l| stay below 2^15, so the conversion cannot overflow, and a
+// coordinate outside ]-1, w_l + 1[ rounds to a pixel outside [0, w_l): the
+// integer test alone gives pixel_at's result.
+__device__ __forceinline__ bool pixel_in(float u0, float v0, int l, int32_t w, int32_t h, int32_t& pu,
+                                         int32_t& pv) {
+  const float s = layer_scale(l);
+  pu = __float2int_rn(__fmul_rn(u0, s));
+  pv = __float2int_rn(__fmul_rn(v0, s));
+  return (uint32_t)pu < (uint32_t)(w >> l) && (uint32_t)pv < (uint32_t)(h >> l);
+}
+
 // One test for all layers: false when (u0, v0) is out of bounds at every
 // layer l < levels (u0 <= -2^(levels-1) or u0 >= w + 2^(levels-1) puts
 // u0 2^-l outside ]-1, w_l + 1[ for each such l; likewise v), so pixel_at

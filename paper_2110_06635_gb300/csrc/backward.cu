@@ -429,7 +429,8 @@ __device__ __forceinline__ void pair_contrib(const DevCam& cam, const PointArgs&
                                              float (&v)[C + 2]) {
   constexpr int GS = g_stride(C);
   int32_t pu, pv;
-  if (!pixel_at(sp[1], sp[2], l, cam.w, cam.h, pu, pv)) return;  // always in bounds for a listed pair
+  // a listed pair's point passed a fuzzy test, so in_pyramid held for the same (u0, v0)
+  if (!pixel_in(sp[1], sp[2], l, cam.w, cam.h, pu, pv)) return;  // always in bounds for a listed pair
   const int32_t wl = cam.w >> l, hl = cam.h >> l;
   const int64_t lb = cam.off[l];
   const int64_t gp = lb + (int64_t)pv * wl + pu;

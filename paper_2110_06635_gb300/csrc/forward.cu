@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_depth(const __grid_constant__ Laun
       for (int l = 0; l < kL; ++l) {
         int32_t pu, pv;
         const bool keep = l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
-        pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
+        pix[l] = (keep && pixel_in(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
       }
       // (an L1-cached read may be stale, but keys only decrease: a stale value
       // can cost an atomic that loses, never skip one that wins, and it can
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, accum_min_blocks<C, kL>())
       for (int l = 0; l < kL; ++l) {
         int32_t pu, pv;
         const bool keep = ((em >> l) & 1u) && l < a.levels && (!a.radius || discard_keep(cam, zd, rw, bt, a.g2, l));
-        pix[l] = (keep && pixel_at(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
+        pix[l] = (keep && pixel_in(u0, v0, l, cam.w, cam.h, pu, pv)) ? pv * (cam.w >> l) + pu : -1;
       }
 #pragma unroll
       for (int l = 0; l < kL; ++l)
