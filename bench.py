@@ -449,14 +449,24 @@ def s8d_kernel_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: i
     }.get(kernel, 0)
 
 
+def bin_table_bytes(w: int, h: int, sms: int, ncam: int = 1) -> int:
+    """Bytes of the binning's [block][tile] table for one camera: one 4-byte
+    entry per block and 32x32-pixel tile, 8 blocks per SM shared by the
+    cameras of a launch (at most 1536 rows in all)."""
+    tiles = ((w + 31) // 32) * ((h + 31) // 32)
+    rows = min((sms * 8 + ncam - 1) // ncam, (1536 + ncam - 1) // ncam)
+    return rows * tiles * 4
+
+
 def implementation_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_out: int,
-                         n_vis: int | None = None) -> int:
+                         n_vis: int | None = None, bin_table: int = 0) -> int:
     """What one launch of this implementation must move (every buffer it
     touches read or written once), including its own records -- the keys it
     reads back, the backward's 16 B pixel records and pixel-major gradient,
     the layer masks and the binning lists.  Not algorithmic bytes: reported
     beside them to show where the design adds traffic (n points, px pyramid
-    pixels, c channels, n_vis points in Lambda of at least one layer)."""
+    pixels, c channels, n_vis points in Lambda of at least one layer,
+    bin_table bytes of the binning's block table)."""
     gs = c if c <= 2 else (c + 3) // 4 * 4
     nv = n if n_vis is None else n_vis
     return {
@@ -465,7 +475,7 @@ def implementation_bytes(kernel: str, n: int, px: int, c: int, s_feat: int, s_ou
         "accumulate": n * (12 + 1 + c * s_feat + 4) + px * (8 + 2 * (4 + 4 * c)),  # xyz, byte, tau -> mask; keys; RMW count+sums
         "normalize": px * (4 + 4 * c + c * s_out),              # read count, sums; write image
         "bwd_prepass": px * (8 + 4 + 4 * c + 4 * c + 16 + 4 * gs),  # key, count, sums, G -> info, G'
-        "bwd_bin": n * 8 + nv * 4,                                    # masks twice -> list
+        "bwd_bin": n * 8 + nv * 4 + 2 * bin_table,                    # masks twice -> list; table written, read
         # list, mask, xyz, tau -> grads of the visible points; pixel records; masks -> zero grads of the rest
         "bwd_points": nv * (4 + 4 + 12 + c * s_feat + 4 * c + 12) + px * (16 + 4 * gs) + n * 4 + (n - nv) * (4 * c + 12),
         "bwd_reduce": 0,
@@ -550,6 +560,7 @@ class Workload:
         self.gpose = torch.zeros((1, 6), dtype=torch.float32, device=device)
         self.gintr = torch.zeros((1, 6), dtype=torch.float32, device=device)
         self.px = adop.pyramid_offsets(cam.w, cam.h, LEVELS)[-1]
+        self.bin_table = bin_table_bytes(cam.w, cam.h, torch.cuda.get_device_properties(device).multi_processor_count)
         self.s_feat = 2 if feat_dtype == "bf16" else 4
         self._prepare()
 
@@ -966,7 +977,8 @@ def bench_large_fwd_bwd(device, sc, steps: int, warmup: int, flush) -> dict:
                    "roofline": kernel_roofline(ks, wl.n, wl.px, wl.c, wl.s_feat, wl.s_feat, n_vis, peak, peak_kind,
                                                recorded=False),
                    "step_bytes_implementation": sum(implementation_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, wl.s_feat,
-                                                                         n_vis) * ks[k][0] for k in ks) // steps,
+                                                                         n_vis, wl.bin_table) * ks[k][0]
+                                                    for k in ks) // steps,
                    "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in ks.items()}}
         del wl, step
         torch.cuda.empty_cache()
@@ -1184,8 +1196,8 @@ def main():
     roofline = kernel_roofline(ks, wl.n, wl.px, wl.c, wl.s_feat, 2, wl.n_vis, peak, peak_kind)
     kernel_ms = {k: round(v[1] / v[0], 4) for k, v in ks.items()}
     step_bytes = s8d_step_bytes(wl.n, wl.px, wl.c, wl.s_feat, 2)
-    impl_step_bytes = sum(implementation_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, 2, wl.n_vis) * ks[k][0]
-                          for k in ks) // K
+    impl_step_bytes = sum(implementation_bytes(k, wl.n, wl.px, wl.c, wl.s_feat, 2, wl.n_vis, wl.bin_table) *
+                          ks[k][0] for k in ks) // K
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),

@@ -71,6 +71,11 @@ def test_algorithmic_bytes_model():
     assert bench.implementation_bytes("bwd_points", n, px, c, 2, 2, 400) == \
         400 * (4 + 4 + 12 + 16 + 32 + 12) + px * 48 + n * 4 + 600 * (32 + 12)
     assert bench.implementation_bytes("bwd_bin", n, px, c, 2, 2, 400) == n * 8 + 400 * 4
+    # the binning's block table: 8 blocks per SM (at most 1536 rows in all) x 32x32 tiles, written and read once
+    assert bench.bin_table_bytes(1920, 1080, 152) == 1216 * 60 * 34 * 4
+    assert bench.bin_table_bytes(1920, 1080, 152, ncam=16) == 76 * 60 * 34 * 4
+    assert bench.bin_table_bytes(1920, 1080, 400, ncam=2) == 768 * 60 * 34 * 4
+    assert bench.implementation_bytes("bwd_bin", n, px, c, 2, 2, 400, 1000) == n * 8 + 400 * 4 + 2000
 
 
 def test_clock_summary_merges_nvidia_smi_and_nvml():
