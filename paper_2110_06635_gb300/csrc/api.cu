@@ -352,6 +352,11 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 void set_last_error(const char* msg) { g_last_error = msg; }
 
+bool& pdl_on() {
+  static thread_local bool on = true;
+  return on;
+}
+
 int prof_begin(const char* name, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return -1;
@@ -508,6 +513,7 @@ adop_status adop_render_forward(const adop_points* pts, const adop_camera* cams,
   const WsLayout L = layout(pts, cams, n_cam, params);
   if ((st = validate_ws(workspace, workspace_bytes, L.total)) != ADOP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const PdlScope pdl(pdl_for_points(pts->n, n_cam < kMaxCamsPerLaunch ? n_cam : kMaxCamsPerLaunch));
   char* ws = static_cast<char*>(workspace);
   for (int k0 = 0; k0 < n_cam; k0 += kMaxCamsPerLaunch) {
     const int nc = (n_cam - k0) < kMaxCamsPerLaunch ? (n_cam - k0) : kMaxCamsPerLaunch;
@@ -533,6 +539,7 @@ adop_status adop_render_backward(const adop_points* pts, const adop_camera* cams
     return fail(ADOP_ERR_INVALID_ARG, "grad_xyz must be 4-byte aligned");
   if ((st = check_grad_feat_dtype(params, n_cam)) != ADOP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const PdlScope pdl(pdl_for_points(pts->n, n_cam < kMaxCamsPerLaunch ? n_cam : kMaxCamsPerLaunch));
   char* ws = static_cast<char*>(workspace);
   const bool assign = (params->flags & ADOP_FLAG_GRAD_ASSIGN) != 0;
   int mode = (n_cam == 1) ? (assign ? kGradAssign : kGradAccumulate) : kGradAtomic;
@@ -637,6 +644,7 @@ adop_status adop_render_backward_noalloc(const adop_points* pts, const adop_came
   char* ws = nullptr;
   if ((st = noalloc_scratch(&ws)) != ADOP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const PdlScope pdl(pdl_for_points(pts->n, n_cam < kMaxCamsPerLaunch ? n_cam : kMaxCamsPerLaunch));
   const bool assign = (params->flags & ADOP_FLAG_GRAD_ASSIGN) != 0;
   const int mode = (n_cam == 1) ? (assign ? kGradAssign : kGradAccumulate) : kGradAtomic;
   cudaError_t e;

@@ -19,16 +19,35 @@ constexpr int kBinSmemTiles = 8192;
 constexpr int kBinTableBlocks = 1536;
 inline int bin_table_rows(int ncam) { return (kBinTableBlocks + ncam - 1) / ncam; }
 
+// Whether launch_pdl launches programmatically on the calling thread (default
+// on); a PdlScope sets it for the launches of one API call.  Every kernel
+// triggers its dependents as it starts, so the next grid is placed on the SMs
+// during this grid's last wave and waits there.  That hides the launch gaps
+// of a step of short kernels (5M-point view: 0.4240 -> 0.4193 ms), but where
+// every block runs many grid-stride iterations the waiting blocks sit through
+// a long, uneven last wave (120M-point frame: 2.305 -> 2.513 ms), so calls
+// with more than kPdlMaxPointWork point-camera pairs launch in plain stream
+// order.
+bool& pdl_on();
+struct PdlScope {
+  bool prev;
+  explicit PdlScope(bool on) : prev(pdl_on()) { pdl_on() = on; }
+  ~PdlScope() { pdl_on() = prev; }
+};
+constexpr int64_t kPdlMaxPointWork = (int64_t)1 << 25;
+inline bool pdl_for_points(int64_t n, int ncam) { return n * (int64_t)ncam <= kPdlMaxPointWork; }
+
 // Launches kernel k on stream s as a programmatic dependent of the work before
-// it in the stream.  The kernel must call pdl_entry() before its first memory
-// access (a CPU test checks every kernel launched this way); it then runs in
-// stream order, while its launch overlaps the end of the previous kernel.  In
-// a captured CUDA graph the dependency becomes a programmatic edge.
+// it in the stream (while pdl_on()).  The kernel must call pdl_entry() before
+// its first memory access (a CPU test checks every kernel launched this way);
+// it then runs in stream order, while its launch overlaps the end of the
+// previous kernel.  In a captured CUDA graph the dependency becomes a
+// programmatic edge.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_on() ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;

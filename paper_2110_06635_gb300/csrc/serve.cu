@@ -219,6 +219,7 @@ void Server::launch_locked() {
     a.a1 = 1.0f + cfg.alpha;
     a.flags = cfg.flags;
     cudaStream_t st = streams[s];
+    const PdlScope pdl(pdl_for_points(a.n, a.ncam));
     cudaError_t e = launch_clear(lc, a, c, st);
     if (e == cudaSuccess) e = launch_depth(lc, a, st);
     if (e == cudaSuccess) e = launch_accum(lc, a, c, feat_dtype, st);
