@@ -247,3 +247,35 @@ def test_layer_mask_buffer_only_4_byte_aligned(adop, orc):
     assert_close(out[1].cpu().numpy(), r["dxyz"], RTOL_GRAD, "dL/dx")
     assert_reduced(out[2].cpu().numpy()[0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
     assert_reduced(out[3].cpu().numpy()[0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
+
+
+@pytest.mark.gpu
+def test_position_gradient_buffer_only_4_byte_aligned(adop, orc):
+    """The ABI asks only 4-byte alignment of dL/dx: a buffer 4 bytes past a
+    16-byte boundary and one on it give the oracle's results, the zero
+    gradients of the points in no Lambda included (filled with NaN before the
+    call, so that a point left unwritten shows; a point count that is not a
+    multiple of 32, so that the last warp's points are partly out of range)."""
+    import torch
+    from parity import assert_reduced
+    sc = scenes.tiny_spheres(20011, 8, seed=77)
+    cams = [scenes.tiny_camera()]
+    G = [scenes.upstream_grad(c.w, c.h, 4, sc.c, 78) for c in cams]
+    r = oracle_run(orc, sc, cams, "f32", grads=G)
+    assert np.sum(~np.any(r["dfeat"] != 0, axis=1)) > 64  # points in no Lambda, whole chunks of them included
+    dev = "cuda"
+    pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+    params = adop.Params(4, 0.01, 1e-3, None, adop.ADOP_FLAG_GRAD_ASSIGN)
+    for offset in (0, 1):  # floats past a 256-byte aligned start: 16-byte and 4-byte aligned
+        fr = adop.Frame.alloc(cams[0], sc.c, 4, torch.float32, True, dev, sc.n)
+        ws = adop.alloc_workspace(pts, cams, params, None, dev)
+        adop.adop_render_forward(pts, cams, params, [fr], ws)
+        gx = torch.full((sc.n * 3 + 4,), float("nan"), device=dev)[offset:offset + sc.n * 3].view(sc.n, 3)
+        assert gx.data_ptr() % 16 == 4 * offset
+        out = [torch.full((sc.n, sc.c), float("nan"), device=dev), gx,
+               torch.zeros((1, 6), device=dev), torch.zeros((1, 6), device=dev)]
+        adop.adop_render_backward(pts, cams, params, [fr], [[torch.from_numpy(x).to(dev) for x in G[0]]], *out,
+                                  ws)
+        assert_close(out[0].cpu().numpy(), r["dfeat"], RTOL_GRAD, "dL/dtau")
+        assert_close(out[1].cpu().numpy(), r["dxyz"], RTOL_GRAD, "dL/dx")
+        assert_reduced(out[2].cpu().numpy()[0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
