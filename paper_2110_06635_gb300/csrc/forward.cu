@@ -66,6 +66,10 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
   pdl_entry();
   const DevCam& cam = cams.c[blockIdx.y];
   const int64_t total = cam.off[a.levels];
+  // a pixel's sums as 256-bit stores (one full sector each) where C % 8 == 0
+  // and acc is 32-byte aligned -- the workspace's always is, a caller's frame
+  // need only be 16-byte aligned (23.1 -> 22.2 us on the 1080p step)
+  const bool v8 = (C % 8 == 0) && (((uintptr_t)cam.acc & 31u) == 0u);
   int lc = 0;  // the layer of g: g only grows, so its layer only advances
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -75,7 +79,10 @@ __global__ void __launch_bounds__(kThreads) k_clear(const __grid_constant__ Laun
     cam.key[l][p] = ~0ull;
     cam.cnt[l][p] = 0u;
     float* acc = cam.acc + g * C;
-    if constexpr (C % 4 == 0) {
+    if (v8) {
+      const float z[C] = {};
+      store_row<C>(acc, z);
+    } else if constexpr (C % 4 == 0) {
 #pragma unroll
       for (int v = 0; v < C / 4; ++v) reinterpret_cast<float4*>(acc)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {

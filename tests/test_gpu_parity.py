@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import scenes
-from parity import RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run, torch_dtype
+from parity import RTOL_FEAT_F32, RTOL_GRAD, assert_close, compare, epilogue_decidable_grads, gpu_run, oracle_run, torch_dtype
 
 pytestmark = pytest.mark.gpu
 
@@ -247,6 +247,32 @@ def test_layer_mask_buffer_only_4_byte_aligned(adop, orc):
     assert_close(out[1].cpu().numpy(), r["dxyz"], RTOL_GRAD, "dL/dx")
     assert_reduced(out[2].cpu().numpy()[0], r["dpose"][0], r["dpose_abs"][0], what="dL/dxi")
     assert_reduced(out[3].cpu().numpy()[0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
+
+
+def test_sum_buffer_only_16_byte_aligned(adop, orc):
+    """The ABI asks 16-byte alignment of a frame's per-pixel sums: with C = 8
+    the clear pass uses 256-bit stores only where the sums are 32-byte aligned;
+    a buffer 16 bytes past a 32-byte boundary gives the oracle's keys, counts
+    and images, the same as an aligned one."""
+    import torch
+    sc = scenes.tiny_spheres(20000, 8, seed=79)
+    cams = [scenes.tiny_camera()]
+    r = oracle_run(orc, sc, cams, "f32")
+    dev = "cuda"
+    pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+    params = adop.Params(4, 0.01, 1e-3, None, 0)
+    for offset in (0, 4):  # floats past a 256-byte aligned start
+        fr = adop.Frame.alloc(cams[0], sc.c, 4, torch.float32, True, dev)
+        px = fr.key.numel()
+        fr.acc = torch.full((px * sc.c + 8,), float("nan"), device=dev)[offset:offset + px * sc.c]
+        assert fr.acc.data_ptr() % 32 == 4 * offset
+        ws = adop.alloc_workspace(pts, cams, params, None, dev)
+        for _ in range(2):  # the second forward clears what the first accumulated
+            adop.adop_render_forward(pts, cams, params, [fr], ws)
+        assert np.array_equal(fr.key.cpu().numpy().view(np.uint64), r["keys"][0])
+        assert np.array_equal(fr.count.cpu().numpy().view(np.uint32), r["cnt"][0])
+        img = np.concatenate([im.cpu().numpy().ravel() for im in fr.images])
+        assert_close(img, r["img"][0], RTOL_FEAT_F32, "images")
 
 
 @pytest.mark.gpu
