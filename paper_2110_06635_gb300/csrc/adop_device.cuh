@@ -350,6 +350,26 @@ __device__ __forceinline__ void load_feat(const T* __restrict__ feat, int64_t i,
   }
 }
 
+// load_feat with streaming loads (evict-first), for a last read.
+template <int C, typename T>
+__device__ __forceinline__ void load_feat_last(const T* __restrict__ feat, int64_t i, float (&f)[C]) {
+  constexpr int kBytes = C * (int)sizeof(T);
+  const T* row = feat + i * C;
+  if constexpr (kBytes % 16 == 0) {
+    constexpr int kVec = kBytes / 16;
+    constexpr int kPer = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) {
+      uint4 raw = __ldcs(reinterpret_cast<const uint4*>(row) + v);
+      const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) f[v * kPer + k] = to_f32<T>(e[k]);
+    }
+  } else {
+    load_feat<C, T>(feat, i, f);
+  }
+}
+
 // The descriptors of point i as linear FP32 values: stored values, or exp of
 // them for logarithmic descriptors (converted during rasterization, Sec. 3.2).
 template <int C, typename T>
