@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="a few steps, no extras (for ncu)")
+    ap.add_argument("--profile-large", action="store_true",
+                    help="only the 120M-point forward + backward in BF16, a few steps (for an ncu launch list)")
     ap.add_argument("--no-train", action="store_true", help="skip the 16-camera training step")
     ap.add_argument("--no-discard", action="store_true", help="skip the stochastic-discarding variant")
     ap.add_argument("--no-env", action="store_true", help="skip the environment-map variant")
@@ -936,7 +938,7 @@ def bench_training_step(device, steps: int = 5, warmup: int = 3) -> dict:
     return out
 
 
-def bench_large_fwd_bwd(device, sc, steps: int, warmup: int, flush) -> dict:
+def bench_large_fwd_bwd(device, sc, steps: int, warmup: int, flush, dtypes=("bf16", "f32")) -> dict:
     """Forward + backward of one 1920x1080 view of the 120M-point cloud (the
     large scene's first path camera), C = 4 descriptors stored in BF16 and in
     FP32, gradients to descriptors, positions, pose and intrinsics: the same
@@ -953,7 +955,7 @@ def bench_large_fwd_bwd(device, sc, steps: int, warmup: int, flush) -> dict:
     out = {"workload": f"{sc.n} points on 500 surfaces in a 100 m box, C=4, one 1920x1080 view of the "
                        "60-frame path, 4 layers, fwd+bwd to tau, x, pose, intrinsics",
            "points": sc.n, "resolution": "1920x1080"}
-    for dt in ("bf16", "f32"):
+    for dt in dtypes:
         wl = Workload(sc.n, dt, device, scene=sc, cam=cam)
         for _ in range(warmup):
             wl.step(sp)
@@ -1183,6 +1185,15 @@ def main():
         return
     if args.impl == "reference":
         return main_reference(args)
+    if args.profile_large:
+        import torch
+        import scenes
+        torch.cuda.set_device(0)
+        flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda:0")
+        sc_large, _ = scenes.config(4)
+        res = bench_large_fwd_bwd("cuda:0", sc_large, args.steps, args.warmup, flush_buf.zero_, dtypes=("bf16",))
+        print(json.dumps({"large_scene_fwd_bwd": res}))
+        return
     dist, rank, world = dist_setup()
     results, clocks, device = run_ours(args, dist, rank, world)
     bf = results["bf16"]
