@@ -249,6 +249,35 @@ def test_layer_mask_buffer_only_4_byte_aligned(adop, orc):
     assert_reduced(out[3].cpu().numpy()[0], r["dintr"][0], r["dintr_abs"][0], what="dL/dK")
 
 
+def test_layer_masks_match_the_oracle(adop, orc):
+    """The forward's per-point layer mask (include/adop.h, adop_frame.vis,
+    bits 0-7) equals the oracle's fuzzy-test membership bit for bit: the
+    point passes z <= f32(z_min (1 + alpha)) at its layer-l pixel, with z_min
+    from the oracle's keys; a point count that is not a multiple of 32."""
+    import torch
+    sc = scenes.tiny_spheres(20003, 8, seed=81)
+    cam = scenes.tiny_camera()
+    f = orc.forward(sc.xyz, sc.feat, cam, 4, 0.01, 1e-3)
+    keys = [k.reshape(-1) for k in f.layer_keys()]
+    a1 = np.float32(1.01)
+    mask = np.zeros(sc.n, np.uint32)
+    for l in range(4):
+        p = f.pix[:, l]
+        ok = p >= 0
+        zmin = (keys[l][np.where(ok, p, 0)] >> np.uint64(32)).astype(np.uint32).view(np.float32)
+        inl = ok & (f.z <= np.float32(zmin * a1))  # FP32 product, rounded once
+        mask |= inl.astype(np.uint32) << np.uint32(l)
+    assert (mask == 0).any() and (mask != 0).any() and (mask > 1).any()
+    dev = "cuda"
+    pts = adop.Points(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.feat).to(dev))
+    params = adop.Params(4, 0.01, 1e-3, None, 0)
+    fr = adop.Frame.alloc(cam, sc.c, 4, torch.float32, True, dev, sc.n)
+    ws = adop.alloc_workspace(pts, [cam], params, None, dev)
+    adop.adop_render_forward(pts, [cam], params, [fr], ws)
+    vis = fr.vis.cpu().numpy().view(np.uint32)
+    assert np.array_equal(vis & 0xFF, mask)
+    assert np.all((vis >> 8)[mask == 0] == 0)  # no tile for a point in no Lambda
+
 def test_sum_buffer_only_16_byte_aligned(adop, orc):
     """The ABI asks 16-byte alignment of a frame's per-pixel sums: with C = 8
     the clear pass uses 256-bit stores only where the sums are 32-byte aligned;
