@@ -460,16 +460,16 @@ __device__ __forceinline__ void pair_contrib(const DevCam& cam, const PointArgs&
       v[C] = g_u * sc;
       v[C + 1] = g_v * sc;
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int c = 0; c < C; ++c) v[c] = G[c] * ip.w;  // ip.w = f32(1/|Lambda|)
-  if (spatial_out) {
-    float g_u, g_v;
-    spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, sp[0], a.a1, sp + 6, g_u, g_v, pol);  // tau read from shared memory
-    const float sc = layer_scale(l);
-    v[C] = g_u * sc;
-    v[C + 1] = g_v * sc;
+    for (int c = 0; c < C; ++c) v[c] = G[c] * ip.w;  // ip.w = f32(1/|Lambda|)
+    if (spatial_out) {
+      float g_u, g_v;
+      spatial_grad<C>(cam, info, lb, pu, pv, wl, hl, sp[0], a.a1, sp + 6, g_u, g_v, pol);  // tau read from shared memory
+      const float sc = layer_scale(l);
+      v[C] = g_u * sc;
+      v[C + 1] = g_v * sc;
+    }
   }
 }
 
